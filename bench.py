@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the multiple-time-origin MSD + autocorrelation path.
+
+One step = MSD of a positions array + autocorrelation of a velocities array
+(the two correlations of Eq. 5 and Eq. 4), then the running Green-Kubo
+integral of the autocorrelation and the Einstein slope of the MSD, all on the
+GPU through the C ABI.  Metric: atom.origin.lag updates per second, where an
+update is one (atom, origin, lag) triple; MSD and autocorrelation updates are
+counted separately and summed.
+
+Default workload: water scale, N = 32768 atoms (3-site molecules), T = 10000
+frames, tau_max = 2000, origin stride 1; positions are a random walk
+(sigma = 0.005 nm per axis per frame, 5 nm box), velocities an OU process
+(gamma = 0.05 per frame, sigma = 1).  Both arrays (3.93 GB each) are larger
+than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--method M]
+       [--impl reference]   (times the FP64 CPU oracle instead)
+Under torchrun each rank runs its own instance (seed + rank) with no
+exchange between ranks (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "water": dict(N=32768, T=10000, tau_max=2000, stride=1, sigma=0.005, box=5.0, gamma=0.05,
+                  sites=3, dt=1.0,
+                  label="water-scale MSD + VACF + GK + Einstein: N=32768 (3-site molecules), "
+                        "T=10000, tau_max=2000, stride 1"),
+    "mid": dict(N=8192, T=5000, tau_max=1000, stride=1, sigma=0.005, box=5.0, gamma=0.05, sites=3,
+                dt=1.0, label="mid-size MSD + VACF + GK + Einstein: N=8192 (3-site molecules), "
+                              "T=5000, tau_max=1000, stride 1 (profiling case)"),
+    "small": dict(N=512, T=1000, tau_max=500, stride=1, sigma=0.01, box=3.0, gamma=0.1, sites=1,
+                  dt=1.0, label="small MSD + VACF: N=512, T=1000, tau_max=500, stride 1"),
+}
+
+
+def updates(N, T, tau_max, s):
+    tau = np.arange(tau_max + 1, dtype=np.int64)
+    return int(N * ((T - 1 - tau) // s + 1).sum())
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_identifier(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return dev
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_sample(xh, vh, wl, target_s):
+    """Time the FP64 oracle on a bounded sample of the workload's lags."""
+    import oracle
+    T, tm, s = wl["T"], wl["tau_max"], wl["stride"]
+    N = xh.shape[1]
+    cores = oracle.default_threads()
+    # calibrate on two lags, then size the sample to about target_s seconds
+    probe = np.array([1, tm], dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.msd(xh, stride=s, lags=probe)
+    t_probe = time.perf_counter() - t0
+    n_lags = int(max(2, min(tm + 1, target_s / max(t_probe, 1e-3))))
+    lags = np.unique(np.linspace(0, tm, n_lags).astype(np.int64))
+    t0 = time.perf_counter()
+    oracle.msd(xh, stride=s, lags=lags)
+    oracle.acf(vh, stride=s, lags=lags)
+    el = time.perf_counter() - t0
+    n_up = 2 * int(sum(N * ((T - 1 - int(l)) // s + 1) for l in lags))
+    return n_up / el, cores, len(lags), el
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1708_08619_gb300 import synth
+    xh = synth.random_walk_positions(wl["T"], wl["N"], wl["sigma"], wl["box"], synth.BASE_SEED,
+                                     sites_per_molecule=wl["sites"])
+    vh = synth.ou_velocities(wl["T"], wl["N"], wl["gamma"], 1.0, synth.BASE_SEED + 1)
+    per_step = float(os.environ.get("TCORR_REF_STEP_S", "3.0"))
+    for _ in range(args.warmup):
+        oracle_sample(xh, vh, wl, per_step / 4)
+    rates, tot_t, cores, nl = [], 0.0, 1, 0
+    for _ in range(args.steps):
+        r, cores, nl, el = oracle_sample(xh, vh, wl, per_step)
+        rates.append(r)
+        tot_t += el
+    value = float(statistics.median(rates))
+    sample = (f"per step: MSD and VACF at {nl} evenly spaced lags in [0, {wl['tau_max']}], all "
+              f"atoms and origins, on the full water-scale arrays (numpy-drawn, same recipe)")
+    line = {"impl": "reference", "metric": "atom.origin.lag updates/s (MSD+ACF)", "value": value,
+            "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot_t / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["label"], "N": wl["N"], "T": wl["T"], "tau_max": wl["tau_max"],
+                       "stride": wl["stride"], "method": "oracle (FP64 CPU)"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, wl):
+    import torch
+    from paper_1708_08619_gb300 import build as tbuild
+    from paper_1708_08619_gb300 import synth, tcorr
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tbuild.build()
+    tcorr.load()
+
+    N, T, tm, s = wl["N"], wl["T"], wl["tau_max"], wl["stride"]
+    method = args.method
+    x = synth.random_walk_positions_device(T, N, wl["sigma"], wl["box"], synth.BASE_SEED + rank,
+                                           device=dev, sites_per_molecule=wl["sites"])
+    v = synth.ou_velocities_device(T, N, wl["gamma"], 1.0, synth.BASE_SEED + 1000 + rank, device=dev)
+    need = max(tcorr.tcorr_workspace_size(T, N, tm, s, method), 256)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    out_m = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+    out_c = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+    out_gk = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+    out_D = torch.empty(2, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    launches_per_step = 6   # tile + reduce (MSD), tile + reduce (ACF), GK, Einstein
+    if method != "plain":
+        launches_per_step = 2 + 3 + 3 + 2  # see the design doc launch table
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    msd_ms, acf_ms = [], []
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        tcorr.tcorr_msd(x, tm, s, method, out=out_m, ws=ws, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        tcorr.tcorr_acf(v, tm, s, method, out=out_c, ws=ws, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        tcorr.gk_integrate(out_c, wl["dt"], 1.0 / 3.0, out=out_gk, stream=stream)
+        tcorr.einstein_slope(out_m, wl["dt"], 3, out=out_D, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if tcorr.tcorr_status_poll() != 0:
+        raise RuntimeError("device status word set during warm-up")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(gpu_identifier(torch, local))
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    for ev in evs:
+        msd_ms.append(ev[0].elapsed_time(ev[1]))
+        acf_ms.append(ev[1].elapsed_time(ev[2]))
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = start.elapsed_time(end)
+    if tcorr.tcorr_status_poll() != 0:
+        raise RuntimeError("device status word set during the timed region")
+
+    t_step = torch.tensor([elapsed_ms / args.steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t_step.item())
+    u_step = updates(N, T, tm, s) * 2
+    value = u_step * world / (ms_per_step / 1000.0)
+
+    # ---- end to end through the public API from pinned host memory
+    xh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
+    vh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
+    xh.copy_(x)
+    vh.copy_(v)
+    x2 = torch.empty_like(x)
+    v2 = torch.empty_like(v)
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        m = tcorr.correlate_host("msd", xh, tm, s, method, device=dev, ws=ws, x_dev=x2)
+        c = tcorr.correlate_host("acf", vh, tm, s, method, device=dev, ws=ws, x_dev=v2)
+        return m, c
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        m_host, c_host = e2e_step()   # .to("cpu") synchronises on the result
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = u_step * world / float(t_e2e.item())
+    h2d = 2 * T * N * 3 * 4
+    d2h = 2 * (tm + 1) * 8
+
+    # ---- roofline of the dominant kernel (the MSD band kernel)
+    pk, pk_kind = peaks()
+    u_res = updates(N, T, tm, s)
+    msd_avg_s = statistics.mean(msd_ms) / 1000.0
+    acf_avg_s = statistics.mean(acf_ms) / 1000.0
+    if method == "plain":
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak_ops = 152 * 128 * sm_mhz * 1e6 / 1e12     # FP32 lane-ops/s (T)
+        achieved = 6.0 * u_res / msd_avg_s / 1e12      # 3 FSUB + 3 FFMA per update
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "plain_tile_kernel<MSD>",
+                "note": f"FP32 lane-ops (FSUB, FFMA) per s; peak = 152 SMs x 128 lanes x "
+                        f"{sm_mhz:.0f} MHz ({pk_kind} max clock); time includes the lag reduce"}
+    else:
+        flops = 6.0 * u_res   # useful Gram flops: 3 MACs per update
+        peak_t = pk.get("bf16_tflops", 1900.0)
+        achieved = flops / msd_avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
+                "frac": achieved / peak_t, "traffic": None, "kernel": "gram_band_tc<MSD>",
+                "note": f"useful Gram FLOPs (6 per update) / MSD call time vs {pk_kind} "
+                        f"bf16 dense burst peak; issued tensor FLOPs are 3x (split) plus band waste"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        xhn = xh.numpy()
+        vhn = vh.numpy()
+        r, cores, nl, el = oracle_sample(xhn, vhn, wl, float(os.environ.get("TCORR_CPU_S", "12")))
+        cpu = {"value": r, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"MSD and VACF at {nl} evenly spaced lags in [0, {tm}], all atoms and "
+                         f"origins of the same arrays; {el:.1f} s"}
+
+    dtype = {"plain": "f32", "fp16x3": "f16x3 (f32 accumulate)", "bf16x3": "bf16x3 (f32 accumulate)",
+             "bf16x4": "bf16x4 (f32 accumulate)", "tf32x3": "tf32x3 (f32 accumulate)"}.get(method, method)
+    line = {"metric": "atom.origin.lag updates/s (MSD+ACF)", "value": value, "unit": "updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": wl["label"], "N": N, "T": T, "tau_max": tm, "stride": s,
+                       "method": method, "parallelism": f"replica x{world}",
+                       "l2": "inputs larger than L2 (2 x %.2f GB), no flush" % (T * N * 12 / 1e9),
+                       "msd_ms": statistics.mean(msd_ms), "acf_ms": statistics.mean(acf_ms),
+                       "updates_per_step": u_step},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof,
+            "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default=os.environ.get("TCORR_BENCH_METHOD", "plain"))
+    ap.add_argument("--workload", default="water", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    main()

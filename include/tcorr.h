@@ -1,0 +1,184 @@
+/*
+ * tcorr.h -- C ABI of libtcorr.so: multiple-time-origin time correlation of
+ * molecular-dynamics trajectories on one GB300 (sm_103a).
+ *
+ * The operations are those of arXiv 1708.08619, Sec. 3.5 ("Correlation
+ * functions"):
+ *   - the mean square displacement of Eq. 5, computed by the loop nest of
+ *     Algorithms 10/11 (atoms, time intervals, time origins), averaged over
+ *     atoms and over time origins;
+ *   - the time autocorrelation <A(t0).A(t0+tau)> that Eq. 4 integrates,
+ *     computed by the loop nest of Algorithms 8/9;
+ *   - the running Green-Kubo integral of Eq. 4 (the quadrature loop that
+ *     closes Algorithms 8 and 9);
+ *   - the Einstein diffusion constant of Eq. 5.
+ *
+ * Common conventions
+ * ------------------
+ * Trajectory layout: x[T][N][3] float32, frame-major, contiguous (the linear
+ * array of Sec. 2.3), i.e. a T x K row-major matrix with K = 3N.  For the MSD
+ * it holds unwrapped positions (Algorithm 10 starts "from unwrapped
+ * trajectory"); for the autocorrelation it holds the signal A (velocities,
+ * or a per-frame flux such as (Pxy, Pxz, Pyz) with N = 1).
+ *
+ * Origins and lags: origins are t0 = 0, s, 2s, ... (stride s >= 1; s = 1 uses
+ * every frame as the paper does); lags are tau = 0 .. tau_max with
+ * 0 <= tau_max <= T-1.  For lag tau the origins used are those with
+ * t0 + tau <= T-1; there are n_o(tau) = floor((T-1-tau)/s) + 1 of them.
+ *
+ * Normalisation: every per-lag output is divided by N * n_o(tau) (the average
+ * over atoms and origins).  The paper leaves the normalisation unstated; this
+ * is the textbook estimator it cites for Eq. 5.
+ *
+ * Memory: every pointer argument prefixed d_ is a device pointer on the
+ * current CUDA device; h_ is a host pointer.  The caller owns every buffer.
+ * The library allocates no device memory: scratch space is the caller's
+ * workspace d_ws of at least tcorr_workspace_size(...) bytes, 256-byte
+ * aligned.  Its contents on entry do not matter and are undefined on exit.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls enqueue work and return without synchronising, so a
+ * returned TCORR_OK means "validated and enqueued".  Buffers must stay valid
+ * until the stream reaches the work.  Two calls that share a workspace must be
+ * ordered on the GPU (same stream, or events).
+ *
+ * Errors: argument errors are detected on the host before anything is
+ * enqueued and returned as a tcorr_status; nothing is written in that case.
+ * A CUDA launch failure returns TCORR_ECUDA.  Errors found by a kernel on the
+ * device (a bounded wait that gave up) are recorded in a per-device status
+ * word that tcorr_status_poll() reads and clears; no kernel traps.
+ *
+ * Determinism: for fixed arguments and method, results are bit-identical
+ * from run to run (all cross-tile sums are fixed-order FP64 reductions).
+ */
+#ifndef TCORR_H
+#define TCORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TCORR_OK = 0,
+    TCORR_EINVAL = 1,        /* bad size, null pointer or unknown method        */
+    TCORR_EALIGN = 2,        /* pointer not aligned as documented               */
+    TCORR_ENOMEM = 3,        /* a host allocation failed                        */
+    TCORR_EWORKSPACE = 4,    /* ws_bytes smaller than tcorr_workspace_size()    */
+    TCORR_ECUDA = 5,         /* a CUDA runtime/driver call or launch failed     */
+    TCORR_ETIMEOUT = 6,      /* a device-side bounded wait gave up (status word)*/
+    TCORR_EUNSUPPORTED = 7   /* method cannot run this shape or on this device  */
+} tcorr_status;
+
+typedef enum {
+    /* FP32 SIMT kernel: per-origin differences (MSD) or products (ACF),
+       accumulated in FP32 over bounded segments of K, FP64 across segments
+       and tiles.  Accuracy target: 1e-6 relative per lag. */
+    TCORR_PLAIN = 0,
+    /* tcgen05 tensor-core banded Gram X X^T over K = 3N with split operands:
+       x = hi + lo, products hi.hi + hi.lo + lo.hi (x3) or also lo.lo (x4),
+       FP32 accumulation in TMEM, FP64 per-lag sums.  The MSD is assembled as
+       S(t0) + S(t0+tau) - 2 G(t0, t0+tau) with S(t) = |x_t|^2 in FP64, after
+       referencing positions to frame 0.  Accuracy target: 1e-5 relative to
+       C(0) or MSD(tau_max). */
+    TCORR_TC_TF32X3 = 1,
+    TCORR_TC_BF16X3 = 2,
+    TCORR_TC_BF16X4 = 3,
+    TCORR_TC_FP16X3 = 4,     /* FP16 hi/lo with a power-of-two scale */
+    TCORR_AUTO = 5           /* the library picks (tensor-core when it can) */
+} tcorr_method;
+
+/*
+ * Bytes of device workspace that tcorr_msd / tcorr_acf need for these
+ * arguments and this method.  Returns 0 when the arguments are invalid (the
+ * call itself then reports the error).  Pure host function; no CUDA call.
+ */
+size_t tcorr_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                            int method);
+
+/*
+ * Mean square displacement (Eq. 5; Algorithms 10 and 11):
+ *   d_out[tau] = 1/(N n_o(tau)) sum_i sum_{t0} |x[t0+tau][i] - x[t0][i]|^2,
+ *   tau = 0 .. tau_max.
+ * d_x   : [T][N][3] float32 unwrapped positions, 4-byte aligned.
+ * d_out : tau_max+1 doubles, 8-byte aligned.
+ * d_ws  : workspace of ws_bytes >= tcorr_workspace_size(...) bytes,
+ *         256-byte aligned (may be NULL when that size is 0).
+ * Errors: TCORR_EINVAL (null pointer, T < 1, N < 1, tau_max outside
+ * [0, T-1], stride < 1, unknown method), TCORR_EALIGN, TCORR_EWORKSPACE,
+ * TCORR_EUNSUPPORTED, TCORR_ECUDA.
+ */
+int tcorr_msd(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+              int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Time autocorrelation, the integrand of Eq. 4 (Algorithms 8 and 9):
+ *   d_out[tau] = 1/(N n_o(tau)) sum_i sum_{t0} A[t0][i] . A[t0+tau][i].
+ * Arguments, alignment and errors as tcorr_msd; d_x holds A.
+ */
+int tcorr_acf(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+              int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Running Green-Kubo integral of Eq. 4, trapezoid rule on the frame grid
+ * (the quadrature loop closing Algorithms 8/9, done on the GPU here):
+ *   d_running[0] = 0,
+ *   d_running[k] = prefactor * sum_{j=1..k} dt (c[j-1] + c[j]) / 2.
+ * prefactor carries V/(k_B T) (and 1/3 to average three components).
+ * d_c, d_running: n doubles (n >= 1), 8-byte aligned; they may not overlap.
+ * The prefix sum is evaluated in a fixed order (deterministic).
+ * Errors: TCORR_EINVAL, TCORR_EALIGN, TCORR_ECUDA.
+ */
+int gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
+                 double *d_running, void *stream);
+
+/*
+ * Einstein relation (Eq. 5): with t = tau dt, d_D[0] = b / (2 dim) where b is
+ * the ordinary least-squares slope of d_msd[tau] against t over
+ * tau in [lo, hi]; d_D[1] = d_msd[hi] / (2 dim hi dt) (the literal ratio).
+ * Needs 0 <= lo < hi < n, dim >= 1, dt > 0.  d_D: 2 doubles.
+ * Errors: TCORR_EINVAL, TCORR_EALIGN, TCORR_ECUDA.
+ */
+int einstein_slope(const double *d_msd, int64_t n, double dt, int dim, int64_t lo,
+                   int64_t hi, double *d_D, void *stream);
+
+/* One entry of a batch: kind 0 = MSD, 1 = autocorrelation. */
+typedef struct {
+    int kind;
+    const float *d_x;        /* [T][N][3] float32 on the device */
+    int64_t T, N, tau_max, stride;
+    double *d_out;           /* tau_max+1 doubles on the device */
+} tcorr_instance;
+
+/*
+ * Many independent instances (trajectories, atom selections, signals of
+ * uneven T, N, tau_max; Eq. 5 averages "over all the atoms in a given
+ * subclass", so a subclass is an instance) in one call.  Each instance's
+ * result equals what tcorr_msd / tcorr_acf would return for it.
+ * h_items: host array of count entries; each is validated as tcorr_msd does.
+ * Workspace: tcorr_batch_workspace_size(...) bytes.
+ */
+size_t tcorr_batch_workspace_size(const tcorr_instance *h_items, int count, int method);
+int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws,
+                size_t ws_bytes, void *stream);
+
+/*
+ * Synchronises `stream`, then returns and clears the current device's status
+ * word: TCORR_OK, or TCORR_ETIMEOUT if a kernel's bounded wait gave up since
+ * the last poll, or TCORR_ECUDA if the synchronisation failed.
+ */
+int tcorr_status_poll(void *stream);
+
+/* Human-readable name of a tcorr_status value (static string). */
+const char *tcorr_strerror(int code);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int tcorr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCORR_H */

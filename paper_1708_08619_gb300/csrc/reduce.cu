@@ -1,0 +1,192 @@
+// FP64 kernels that close the path:
+//   lag_reduce   -- fixed-order sum of per-item band-offset partials into the
+//                   per-lag sum D(tau), then the normalisation by N n_o(tau)
+//                   (the "update global MSD array" step of Algorithm 11, done
+//                   deterministically instead of by a race);
+//   gk_integrate -- running trapezoid integral of Eq. 4 (the quadrature loop
+//                   closing Algorithms 8 and 9, which the paper runs on the host);
+//   einstein     -- least-squares slope of the MSD and D = slope / (2d), Eq. 5.
+#include "tcorr_internal.cuh"
+
+namespace tcorr {
+namespace {
+
+struct ReduceArgs {
+    const double *partial;
+    int64_t T, N, s, tau_max;
+    int64_t n_res, n_rows, n_cols, n_groups;
+    int BO, BF, WP;
+    int mode;
+    const double *S_prefix;
+    int64_t prefix_stride;
+    double *out;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// One warp per lag.  Lane l sums terms l, l+32, ... in order; the lanes are
+// then combined by a fixed butterfly, so the result does not depend on timing.
+__global__ void lag_reduce_kernel(ReduceArgs a) {
+    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tau > a.tau_max) return;
+    const int64_t rho = tau % a.s, m = tau / a.s;
+    const int64_t c_lo = m / a.BF;
+    int64_t c_hi = (m + a.BO - 1) / a.BF;
+    if (c_hi > a.n_cols - 1) c_hi = a.n_cols - 1;
+    const int64_t ncs = c_hi - c_lo + 1;
+    const int64_t nterm = a.n_groups * a.n_rows * ncs;
+    double sum = 0.0;
+    for (int64_t t = lane; t < nterm; t += 32) {
+        const int64_t cc = t % ncs;
+        const int64_t rr = (t / ncs) % a.n_rows;
+        const int64_t gg = t / (ncs * a.n_rows);
+        const int64_t c = c_lo + cc;
+        const int64_t item = ((gg * a.n_res + rho) * a.n_rows + rr) * a.n_cols + c;
+        const int64_t w = m - c * a.BF + a.BO - 1;
+        sum += a.partial[item * a.WP + w];
+    }
+    const double D = warp_sum(sum);
+    if (lane == 0) {
+        const int64_t no = n_origins(a.T, a.s, tau);
+        const double denom = static_cast<double>(a.N) * static_cast<double>(no);
+        double v;
+        if (a.mode == 0) {
+            v = D / denom;
+        } else if (tau == 0) {
+            v = 0.0;   // |x - x|^2: exactly zero by definition
+        } else {
+            // P = sum_{o < n_o} S(o s);  Q = sum_{o < n_o} S(o s + tau).
+            // S_prefix row rho' holds prefix sums over S(rho' + j s), j = 0, 1, ...
+            const double *p0 = a.S_prefix;
+            const double P = p0[no];
+            const int64_t qq = tau / a.s;
+            const double *pr = a.S_prefix + (tau % a.s) * a.prefix_stride;
+            const double Q = pr[qq + no] - pr[qq];
+            v = (P + Q - 2.0 * D) / denom;
+        }
+        a.out[tau] = v;
+    }
+}
+
+// Running trapezoid.  One block: thread t owns a contiguous chunk, forms its
+// local running sum, the chunk totals are scanned by thread 0 in order, then
+// each thread adds its offset.  Fixed order throughout.
+constexpr int GK_THREADS = 1024;
+
+__global__ void gk_integrate_kernel(const double *c, int64_t n, double dt, double prefactor,
+                                    double *running) {
+    __shared__ double tot[GK_THREADS];
+    const int t = threadIdx.x;
+    const int64_t nseg = n - 1;                     // increments k = 1 .. n-1
+    const int64_t per = ceil_div(nseg > 0 ? nseg : 1, GK_THREADS);
+    const int64_t b = 1 + t * per;
+    const int64_t e = min(n, b + per);
+    double acc = 0.0;
+    for (int64_t k = b; k < e; ++k) acc += dt * (c[k - 1] + c[k]) / 2.0;
+    tot[t] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double run = 0.0;
+        for (int i = 0; i < GK_THREADS; ++i) {
+            const double v = tot[i];
+            tot[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    double I = tot[t];
+    if (t == 0) running[0] = 0.0;
+    for (int64_t k = b; k < e; ++k) {
+        I += dt * (c[k - 1] + c[k]) / 2.0;
+        running[k] = prefactor * I;
+    }
+}
+
+constexpr int EIN_THREADS = 256;
+
+__device__ double block_sum(double v, double *sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = EIN_THREADS / 2; off > 0; off >>= 1) {
+        if (t < off) sh[t] += sh[t + off];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void einstein_kernel(const double *msd, double dt, int dim, int64_t lo, int64_t hi,
+                                double *D) {
+    __shared__ double sh[EIN_THREADS];
+    const int t = threadIdx.x;
+    const double m = static_cast<double>(hi - lo + 1);
+    double sx = 0.0, sy = 0.0;
+    for (int64_t k = lo + t; k <= hi; k += EIN_THREADS) {
+        sx += static_cast<double>(k) * dt;
+        sy += msd[k];
+    }
+    const double xbar = block_sum(sx, sh) / m;
+    const double ybar = block_sum(sy, sh) / m;
+    double sxy = 0.0, sxx = 0.0;
+    for (int64_t k = lo + t; k <= hi; k += EIN_THREADS) {
+        const double dx = static_cast<double>(k) * dt - xbar;
+        sxy += dx * (msd[k] - ybar);
+        sxx += dx * dx;
+    }
+    const double Sxy = block_sum(sxy, sh);
+    const double Sxx = block_sum(sxx, sh);
+    if (t == 0) {
+        D[0] = (Sxy / Sxx) / (2.0 * dim);
+        D[1] = msd[hi] / (2.0 * dim * static_cast<double>(hi) * dt);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
+                              double *d_out, cudaStream_t st) {
+    ReduceArgs a;
+    a.partial = partial;
+    a.T = p.T;
+    a.N = p.N;
+    a.s = p.s;
+    a.tau_max = p.tau_max;
+    a.n_res = p.n_res;
+    a.n_rows = p.n_rows;
+    a.n_cols = p.n_cols;
+    a.n_groups = p.n_groups;
+    a.BO = p.BO;
+    a.BF = p.BF;
+    a.WP = p.WP;
+    a.mode = fa.mode;
+    a.S_prefix = fa.S_prefix;
+    a.prefix_stride = fa.prefix_stride;
+    a.out = d_out;
+    const int64_t warps = p.tau_max + 1;
+    const int threads = 256;
+    const int64_t blocks = ceil_div(warps * 32, threads);
+    lag_reduce_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
+                                double *d_running, cudaStream_t st) {
+    gk_integrate_kernel<<<1, GK_THREADS, 0, st>>>(d_c, n, dt, prefactor, d_running);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_einstein(const double *d_msd, int64_t n, double dt, int dim, int64_t lo,
+                            int64_t hi, double *d_D, cudaStream_t st) {
+    (void)n;
+    einstein_kernel<<<1, EIN_THREADS, 0, st>>>(d_msd, dt, dim, lo, hi, d_D);
+    return cudaGetLastError();
+}
+
+}  // namespace tcorr

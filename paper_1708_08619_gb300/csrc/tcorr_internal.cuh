@@ -1,0 +1,85 @@
+// Internal declarations shared by the translation units of libtcorr.so.
+//
+// Band tiling of the origin x frame plane (all methods)
+// ----------------------------------------------------
+// Origins are t0 = o*s (o = 0 .. n_orig-1).  A lag tau is split as
+// tau = rho + m*s with residue rho = tau mod s, so the frame t0 + tau equals
+// rho + (o+m)*s: for each residue rho the work is a stride-1 banded
+// cross-correlation between the origin rows X[o*s] and the frame rows
+// X[rho + k*s] (k = 0 .. n_rho-1), restricted to 0 <= k - o <= m_max(rho)
+// with m_max(rho) = floor((tau_max - rho)/s).  For s = 1 there is one residue
+// and this is the plain band |t - t'| <= tau_max of the Gram matrix X X^T.
+//
+// A tile (rho, r, c) covers origins o in [r*BO, r*BO+BO) and frame indices
+// k in [r*BO + c*BF, r*BO + c*BF + BF).  Its entries fall on band offsets
+// m = k - o in [c*BF - BO + 1, c*BF + BF - 1]; the tile stores its per-offset
+// sums in a window of width BO+BF-1 indexed by w = m - c*BF + BO - 1.
+// Work items are (K-group g, rho, r, c), c fastest, so that neighbouring
+// blocks share origin rows and overlapping frame rows in L2.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tcorr.h"
+
+namespace tcorr {
+
+struct BandPlan {
+    int64_t T, N, K;          // frames, atoms, K = 3N
+    int64_t tau_max, s;       // max lag, origin stride
+    int64_t n_orig;           // origins: floor((T-1)/s) + 1
+    int64_t n_res;            // residues that carry lags: min(s, tau_max+1)
+    int64_t m_max0;           // m_max(0) = floor(tau_max / s)
+    int BO, BF;               // tile extent over origins / frame indices
+    int WP;                   // padded window width (>= BO+BF-1)
+    int64_t n_rows, n_cols;   // row tiles, column tiles per row tile
+    int64_t kseg;             // K elements per FP32 accumulation segment
+    int64_t segs_per_item;    // segments one work item walks
+    int64_t n_groups;         // K groups: ceil(ceil(K/kseg)/segs_per_item)
+    int64_t n_items;          // n_groups * n_res * n_rows * n_cols
+};
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// n_o(tau) = floor((T-1-tau)/s) + 1 origins for lag tau.
+__host__ __device__ inline int64_t n_origins(int64_t T, int64_t s, int64_t tau) {
+    return (T - 1 - tau) / s + 1;
+}
+
+// Frame indices available for residue rho: frames rho, rho+s, ... <= T-1.
+__host__ __device__ inline int64_t n_frames_res(int64_t T, int64_t s, int64_t rho) {
+    return rho > T - 1 ? 0 : (T - 1 - rho) / s + 1;
+}
+
+// Build the plan.  `min_items` steers how many K segments one item walks so
+// that the grid has enough blocks to fill the GPU.
+BandPlan make_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int BO, int BF,
+                        int64_t kseg, int64_t min_items);
+
+// Workspace layout helpers (byte offsets, 256-byte aligned).
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------ kernels
+// Plain FP32 path: per-item per-offset partial sums (double) into `partial`
+// ([n_items][WP]).  kind 0 = MSD (differences), 1 = ACF (products).
+cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, double *partial,
+                               cudaStream_t st);
+
+// Fixed-order FP64 reduction of the per-item partials to per-lag sums D(tau),
+// then the normalisation.  mode 0: out = D / (N n_o) (plain MSD and ACF);
+// mode 1: out = (P + Q - 2 D) / (N n_o) using prefix sums of S (Gram MSD).
+struct FinalizeArgs {
+    int mode;
+    const double *S_prefix;   // mode 1: [n_res_prefix][...] see gram code
+    int64_t prefix_stride;    // mode 1: entries per residue row of S_prefix
+};
+cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
+                              double *d_out, cudaStream_t st);
+
+cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
+                                double *d_running, cudaStream_t st);
+cudaError_t launch_einstein(const double *d_msd, int64_t n, double dt, int dim, int64_t lo,
+                            int64_t hi, double *d_D, cudaStream_t st);
+
+}  // namespace tcorr

@@ -129,7 +129,12 @@ def random_walk_positions_device(T: int, N: int, sigma: float, box: float, seed:
 
 def ou_velocities_device(T: int, N: int, gamma: float, sigma: float, seed: int,
                          device="cuda"):
-    """Exact OU recursion (see module docstring) with torch's device RNG."""
+    """Exact OU recursion (see module docstring) with torch's device RNG.
+
+    Frames are drawn in blocks of B: within a block
+    v[k] = phi^k (phi v_prev + kick * sum_{j<=k} phi^-j xi[j]),
+    with B small enough that phi^-B stays below 1e6.
+    """
     torch = _torch()
     g = torch.Generator(device=device)
     g.manual_seed(seed)
@@ -138,11 +143,16 @@ def ou_velocities_device(T: int, N: int, gamma: float, sigma: float, seed: int,
     out = torch.empty((T, N, 3), dtype=torch.float32, device=device)
     v = torch.randn((N, 3), generator=g, device=device, dtype=torch.float64) * sigma
     out[0] = v.to(torch.float32)
-    block = 256
-    for t0 in range(1, T, block):
-        t1 = min(T, t0 + block)
-        xi = torch.randn((t1 - t0, N, 3), generator=g, device=device, dtype=torch.float64)
-        for k in range(t1 - t0):
-            v.mul_(phi).add_(xi[k], alpha=kick)
-            out[t0 + k].copy_(v)
+    B = int(max(1, min(512, math.floor(math.log(1e6) / max(gamma, 1e-12)))))
+    for t0 in range(1, T, B):
+        b = min(B, T - t0)
+        xi = torch.randn((b, N, 3), generator=g, device=device, dtype=torch.float64)
+        k = torch.arange(b, device=device, dtype=torch.float64)
+        xi.mul_((phi ** (-k)).view(b, 1, 1))
+        torch.cumsum(xi, dim=0, out=xi)
+        xi.mul_(kick).add_(phi * v)
+        xi.mul_((phi ** k).view(b, 1, 1))
+        out[t0:t0 + b] = xi.to(torch.float32)
+        v = xi[-1].clone()
+        del xi
     return out

@@ -1,0 +1,216 @@
+"""Python binding of libtcorr.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls
+(``include/tcorr.h``).  Tensors are torch tensors; the binding passes their
+device pointers, allocates outputs and workspace with torch when the caller
+gives none, and passes torch's current CUDA stream.  All arithmetic of the
+path runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing or the tensors are not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PLAIN, TC_TF32X3, TC_BF16X3, TC_BF16X4, TC_FP16X3, AUTO = range(6)
+METHODS = {"plain": PLAIN, "tf32x3": TC_TF32X3, "bf16x3": TC_BF16X3, "bf16x4": TC_BF16X4,
+           "fp16x3": TC_FP16X3, "auto": AUTO}
+STATUS = {0: "TCORR_OK", 1: "TCORR_EINVAL", 2: "TCORR_EALIGN", 3: "TCORR_ENOMEM",
+          4: "TCORR_EWORKSPACE", 5: "TCORR_ECUDA", 6: "TCORR_ETIMEOUT", 7: "TCORR_EUNSUPPORTED"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtcorr.so")
+_lib = None
+
+
+class TcorrError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class TcorrInstance(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d_x", ctypes.c_void_p), ("T", ctypes.c_int64),
+                ("N", ctypes.c_int64), ("tau_max", ctypes.c_int64), ("stride", ctypes.c_int64),
+                ("d_out", ctypes.c_void_p)]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Open libtcorr.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1708_08619_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    i64, vp, dbl, ci, sz = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+    lib.tcorr_workspace_size.argtypes = [i64, i64, i64, i64, ci]
+    lib.tcorr_workspace_size.restype = sz
+    for name in ("tcorr_msd", "tcorr_acf"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, i64, i64, i64, i64, ci, vp, vp, sz, vp]
+        f.restype = ci
+    lib.gk_integrate.argtypes = [vp, i64, dbl, dbl, vp, vp]
+    lib.gk_integrate.restype = ci
+    lib.einstein_slope.argtypes = [vp, i64, dbl, ci, i64, i64, vp, vp]
+    lib.einstein_slope.restype = ci
+    lib.tcorr_batch_workspace_size.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci]
+    lib.tcorr_batch_workspace_size.restype = sz
+    lib.tcorr_batch.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci, vp, sz, vp]
+    lib.tcorr_batch.restype = ci
+    lib.tcorr_status_poll.argtypes = [vp]
+    lib.tcorr_status_poll.restype = ci
+    lib.tcorr_strerror.argtypes = [ci]
+    lib.tcorr_strerror.restype = ctypes.c_char_p
+    lib.tcorr_version.argtypes = []
+    lib.tcorr_version.restype = ci
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _method(m) -> int:
+    return METHODS[m] if isinstance(m, str) else int(m)
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_traj(x):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("x must be a CUDA torch tensor")
+    if x.dtype != torch.float32 or x.dim() != 3 or x.shape[2] != 3 or not x.is_contiguous():
+        raise TypeError("x must be a contiguous float32 tensor of shape [T][N][3]")
+
+
+def tcorr_workspace_size(T: int, N: int, tau_max: int, stride: int = 1, method=AUTO) -> int:
+    return int(load().tcorr_workspace_size(T, N, tau_max, stride, _method(method)))
+
+
+def _alloc_ws(nbytes: int, device):
+    torch = _torch()
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def _corr(fname: str, x, tau_max: int, stride: int, method, out, ws, stream):
+    torch = _torch()
+    _check_traj(x)
+    T, N, _ = x.shape
+    m = _method(method)
+    if out is None:
+        out = torch.empty(tau_max + 1, dtype=torch.float64, device=x.device)
+    need = tcorr_workspace_size(T, N, tau_max, stride, m)
+    if ws is None:
+        ws = _alloc_ws(need, x.device)
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = getattr(load(), fname)(x.data_ptr(), T, N, tau_max, stride, m, out.data_ptr(),
+                                ws_ptr, ws_bytes, _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, fname)
+    return out
+
+
+def tcorr_msd(x, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, stream=None):
+    """MSD(tau), tau = 0..tau_max, of x[T][N][3] (Eq. 5); returns a float64 tensor."""
+    return _corr("tcorr_msd", x, tau_max, stride, method, out, ws, stream)
+
+
+def tcorr_acf(x, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, stream=None):
+    """<A(t0).A(t0+tau)>, tau = 0..tau_max, of A[T][N][3] (Eq. 4 integrand)."""
+    return _corr("tcorr_acf", x, tau_max, stride, method, out, ws, stream)
+
+
+def gk_integrate(c, dt: float, prefactor: float = 1.0, out=None, stream=None):
+    """Running trapezoid integral prefactor * int_0^tau C dt (Eq. 4)."""
+    torch = _torch()
+    if not c.is_cuda or c.dtype != torch.float64 or not c.is_contiguous():
+        raise TypeError("c must be a contiguous float64 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(c)
+    rc = load().gk_integrate(c.data_ptr(), c.numel(), dt, prefactor, out.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "gk_integrate")
+    return out
+
+
+def einstein_slope(msd, dt: float, dim: int = 3, lo: int | None = None, hi: int | None = None,
+                   out=None, stream=None):
+    """[D from the least-squares slope over [lo, hi], D from the ratio at hi] (Eq. 5)."""
+    torch = _torch()
+    if not msd.is_cuda or msd.dtype != torch.float64 or not msd.is_contiguous():
+        raise TypeError("msd must be a contiguous float64 CUDA tensor")
+    n = msd.numel()
+    if hi is None:
+        hi = n - 1
+    if lo is None:
+        lo = -(-(2 * hi) // 10)
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=msd.device)
+    rc = load().einstein_slope(msd.data_ptr(), n, dt, dim, lo, hi, out.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "einstein_slope")
+    return out
+
+
+def make_instances(items):
+    """items: iterable of (kind, x, tau_max, stride, out) -> ctypes array."""
+    items = list(items)
+    arr = (TcorrInstance * len(items))()
+    for i, (kind, x, tau_max, stride, out) in enumerate(items):
+        _check_traj(x)
+        arr[i] = TcorrInstance(kind, x.data_ptr(), x.shape[0], x.shape[1], tau_max, stride,
+                               out.data_ptr())
+    return arr
+
+
+def tcorr_batch_workspace_size(instances, method=AUTO) -> int:
+    return int(load().tcorr_batch_workspace_size(instances, len(instances), _method(method)))
+
+
+def tcorr_batch(instances, method=AUTO, ws=None, stream=None, device=None):
+    """Run every instance of a ``make_instances`` array; outputs are written in place."""
+    torch = _torch()
+    m = _method(method)
+    need = tcorr_batch_workspace_size(instances, m)
+    if ws is None:
+        ws = _alloc_ws(need, device or torch.device("cuda"))
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = load().tcorr_batch(instances, len(instances), m, ws_ptr, ws_bytes, _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_batch")
+
+
+def tcorr_status_poll(stream=None) -> int:
+    return int(load().tcorr_status_poll(_stream_ptr(stream)))
+
+
+def tcorr_version() -> int:
+    return int(load().tcorr_version())
+
+
+def correlate_host(kind: str, x_host, tau_max: int, stride: int = 1, method=AUTO,
+                   device="cuda", ws=None, x_dev=None):
+    """End-to-end call from host memory: copy x to the device, run, copy back.
+
+    ``x_host`` is a (preferably pinned) float32 CPU tensor [T][N][3]; returns a
+    float64 CPU tensor.  ``x_dev`` / ``ws`` may be given to reuse device buffers.
+    """
+    torch = _torch()
+    if x_dev is None:
+        x_dev = torch.empty(x_host.shape, dtype=torch.float32, device=device)
+    x_dev.copy_(x_host, non_blocking=True)
+    f = tcorr_msd if kind == "msd" else tcorr_acf
+    out = f(x_dev, tau_max, stride, method, ws=ws)
+    return out.to("cpu")

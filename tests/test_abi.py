@@ -1,0 +1,127 @@
+"""The C ABI: the library builds, loads, exports every declared symbol, and
+rejects bad arguments on the host before any CUDA work (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1708_08619_gb300 import build as tbuild
+from paper_1708_08619_gb300 import tcorr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = tbuild.build()
+    return tcorr.load(path)
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\([^;{)]*\)\s*;", text):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for want in ("tcorr_msd", "tcorr_acf", "tcorr_batch", "gk_integrate", "einstein_slope",
+                 "tcorr_workspace_size", "tcorr_status_poll"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_version_and_strerror(lib):
+    assert lib.tcorr_version() >= 100
+    for code in range(8):
+        assert lib.tcorr_strerror(code).startswith(b"TCORR_")
+
+
+FAKE_X = 0x10000        # never dereferenced: every call below fails validation first
+FAKE_OUT = 0x20000
+FAKE_WS = 0x30000
+
+
+def call_msd(lib, x=FAKE_X, T=100, N=10, tau_max=50, s=1, method=0, out=FAKE_OUT,
+             ws=FAKE_WS, ws_bytes=0):
+    return lib.tcorr_msd(x, T, N, tau_max, s, method, out, ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(x=None), dict(out=None), dict(T=0), dict(N=0), dict(tau_max=-1), dict(tau_max=100),
+    dict(s=0), dict(method=99), dict(method=-1),
+])
+def test_invalid_arguments(lib, kw):
+    assert call_msd(lib, **kw) == 1   # TCORR_EINVAL
+
+
+def test_misaligned(lib):
+    assert call_msd(lib, x=FAKE_X + 2) == 2
+    assert call_msd(lib, out=FAKE_OUT + 4) == 2
+    assert call_msd(lib, ws=FAKE_WS + 8) == 2
+
+
+def test_workspace_too_small(lib):
+    need = lib.tcorr_workspace_size(100, 10, 50, 1, 0)
+    assert need > 0
+    assert call_msd(lib, ws_bytes=need - 1) == 4
+    assert lib.tcorr_acf(FAKE_X, 100, 10, 50, 1, 0, FAKE_OUT, None, need, None) == 4
+
+
+def test_workspace_size_rejects_invalid(lib):
+    assert lib.tcorr_workspace_size(0, 10, 0, 1, 0) == 0
+    assert lib.tcorr_workspace_size(10, 10, 10, 1, 0) == 0
+    assert lib.tcorr_workspace_size(10, 10, 9, 0, 0) == 0
+    assert lib.tcorr_workspace_size(10, 10, 9, 1, 42) == 0
+
+
+def test_workspace_grows_with_the_band(lib):
+    a = lib.tcorr_workspace_size(10000, 1000, 100, 1, 0)
+    b = lib.tcorr_workspace_size(10000, 1000, 5000, 1, 0)
+    assert b > a > 0
+
+
+def test_gk_and_einstein_validation(lib):
+    assert lib.gk_integrate(None, 10, 1.0, 1.0, FAKE_OUT, None) == 1
+    assert lib.gk_integrate(FAKE_X, 0, 1.0, 1.0, FAKE_OUT, None) == 1
+    assert lib.gk_integrate(FAKE_X + 4, 10, 1.0, 1.0, FAKE_OUT, None) == 2
+    assert lib.gk_integrate(FAKE_X, 10, 1.0, 1.0, FAKE_X + 8, None) == 1   # overlap
+    D = FAKE_OUT
+    assert lib.einstein_slope(FAKE_X, 10, 1.0, 3, 5, 5, D, None) == 1     # hi <= lo
+    assert lib.einstein_slope(FAKE_X, 10, 1.0, 3, 2, 10, D, None) == 1    # hi >= n
+    assert lib.einstein_slope(FAKE_X, 10, 0.0, 3, 2, 9, D, None) == 1     # dt <= 0
+    assert lib.einstein_slope(FAKE_X, 10, 1.0, 0, 2, 9, D, None) == 1     # dim < 1
+
+
+def test_batch_validation(lib):
+    inst = (tcorr.TcorrInstance * 2)()
+    inst[0] = tcorr.TcorrInstance(0, FAKE_X, 100, 10, 50, 1, FAKE_OUT)
+    inst[1] = tcorr.TcorrInstance(2, FAKE_X, 100, 10, 50, 1, FAKE_OUT)   # bad kind
+    assert lib.tcorr_batch(inst, 2, 0, FAKE_WS, 1 << 30, None) == 1
+    inst[1] = tcorr.TcorrInstance(1, FAKE_X, 100, 10, 100, 1, FAKE_OUT)  # tau_max > T-1
+    assert lib.tcorr_batch(inst, 2, 0, FAKE_WS, 1 << 30, None) == 1
+    inst[1] = tcorr.TcorrInstance(1, FAKE_X, 100, 10, 99, 1, FAKE_OUT)
+    need = lib.tcorr_batch_workspace_size(inst, 2, 0)
+    assert need >= lib.tcorr_workspace_size(100, 10, 99, 1, 0)
+    assert lib.tcorr_batch(inst, 2, 0, FAKE_WS, need - 1, None) == 4
+    assert lib.tcorr_batch(inst, 0, 0, FAKE_WS, need, None) == 1
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    torch = pytest.importorskip("torch")
+    x = torch.zeros((10, 2, 3), dtype=torch.float32)
+    with pytest.raises(TypeError):
+        tcorr.tcorr_msd(x, 5)
