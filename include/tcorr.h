@@ -165,6 +165,28 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
                 size_t ws_bytes, void *stream);
 
 /*
+ * Plain FP32 path without a caller workspace: the same result, bit for bit,
+ * as tcorr_msd (kind 0) or tcorr_acf (kind 1) with method TCORR_PLAIN, but
+ * the library allocates nothing and the caller passes no workspace.  The
+ * paper has no counterpart; this entry point is for callers that cannot
+ * allocate device memory, e.g. an analysis hook inside a simulation engine
+ * whose device memory all belongs to the engine's own pool, or a host that
+ * must not call cudaMalloc because it synchronises the device.
+ * Scratch: one fixed 32 MiB array of device memory, held by every GPU that
+ * loads this part of the library until the process exits.  Its device
+ * address is looked up on the first call on each device (with that device
+ * current), so make that first call before any stream capture.  All calls on
+ * a device share the array: calls whose work overlaps on the GPU race.
+ * Limit: the per-item partial sums must fit the array
+ * (8 * 256 * n_items bytes, about 16k band tiles); larger shapes return
+ * TCORR_EWORKSPACE without launching anything.
+ * d_x: [T][N][3] float32, 4-byte aligned; d_out: tau_max+1 doubles, 8-byte
+ * aligned.  Errors: TCORR_EINVAL, TCORR_EALIGN, TCORR_EWORKSPACE, TCORR_ECUDA.
+ */
+int tcorr_plain_static(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max,
+                       int64_t stride, double *d_out, void *stream);
+
+/*
  * Synchronises `stream`, then returns and clears the current device's status
  * word: TCORR_OK, or TCORR_ETIMEOUT if a kernel's bounded wait gave up since
  * the last poll, or TCORR_ECUDA if the synchronisation failed.

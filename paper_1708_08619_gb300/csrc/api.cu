@@ -103,6 +103,17 @@ int run_corr(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
 }
 
 }  // namespace
+
+// The plain path's plan and size check, shared with the fixed-scratch entry
+// point so that both produce bit-identical results for the same arguments.
+BandPlan plain_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
+    return make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg, kMinItems);
+}
+
+bool corr_sizes_valid(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
+    return valid_sizes(T, N, tau_max, s);
+}
+
 }  // namespace tcorr
 
 using namespace tcorr;

@@ -57,6 +57,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tcorr_batch_workspace_size.restype = sz
     lib.tcorr_batch.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci, vp, sz, vp]
     lib.tcorr_batch.restype = ci
+    lib.tcorr_plain_static.argtypes = [ci, vp, i64, i64, i64, i64, vp, vp]
+    lib.tcorr_plain_static.restype = ci
     lib.tcorr_status_poll.argtypes = [vp]
     lib.tcorr_status_poll.restype = ci
     lib.tcorr_strerror.argtypes = [ci]
@@ -190,6 +192,20 @@ def tcorr_batch(instances, method=AUTO, ws=None, stream=None, device=None):
     rc = load().tcorr_batch(instances, len(instances), m, ws_ptr, ws_bytes, _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "tcorr_batch")
+
+
+def tcorr_plain_static(kind: int, x, tau_max: int, stride: int = 1, out=None, stream=None):
+    """Plain path with the library's fixed device scratch (no workspace, nothing allocated
+    by the library); kind 0 = MSD, 1 = autocorrelation."""
+    torch = _torch()
+    _check_traj(x)
+    if out is None:
+        out = torch.empty(tau_max + 1, dtype=torch.float64, device=x.device)
+    rc = load().tcorr_plain_static(kind, x.data_ptr(), x.shape[0], x.shape[1], tau_max, stride,
+                                   out.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_plain_static")
+    return out
 
 
 def tcorr_status_poll(stream=None) -> int:
