@@ -207,9 +207,9 @@ def run_gpu(args, wl):
     out_gk = torch.empty(tm + 1, dtype=torch.float64, device=dev)
     out_D = torch.empty(2, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    launches_per_step = 6   # tile + reduce (MSD), tile + reduce (ACF), GK, Einstein
-    if method != "plain":
-        launches_per_step = 2 + 3 + 3 + 2  # see the design doc launch table
+    # plain: tile + reduce (MSD), tile + reduce (ACF), GK, Einstein
+    # tensor core: split + S prefix + gram + reduce (MSD), split + gram + reduce (ACF), GK, Einstein
+    launches_per_step = 6 if method == "plain" else 9
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     msd_ms, acf_ms = [], []
@@ -318,6 +318,27 @@ def run_gpu(args, wl):
                 "note": f"useful Gram FLOPs (6 per update) / MSD call time vs {pk_kind} "
                         f"bf16 dense burst peak; issued tensor FLOPs are 3x (split) plus band waste"}
 
+    # ---- the plain FP32 kernel on the same arrays, for the tensor-core vs plain comparison
+    plain_cmp = None
+    if method != "plain" and not args.no_plain_compare:
+        ws_p = torch.empty(max(tcorr.tcorr_workspace_size(T, N, tm, s, "plain"), 256), dtype=torch.uint8,
+                           device=dev)
+        tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
+        tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
+            tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p_ms = e0.elapsed_time(e1) / reps
+        plain_cmp = {"method": "plain", "ms_per_step_msd_acf": p_ms,
+                     "updates_per_s": u_step / (p_ms / 1000.0),
+                     "speedup_of_timed_method": (u_step / (p_ms / 1000.0)) and value / (u_step / (p_ms / 1000.0))}
+        del ws_p
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         xhn = xh.numpy()
@@ -337,7 +358,7 @@ def run_gpu(args, wl):
                        "method": method, "parallelism": f"replica x{world}",
                        "l2": "inputs larger than L2 (2 x %.2f GB), no flush" % (T * N * 12 / 1e9),
                        "msd_ms": statistics.mean(msd_ms), "acf_ms": statistics.mean(acf_ms),
-                       "updates_per_step": u_step},
+                       "updates_per_step": u_step, "plain_comparison": plain_cmp},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -357,7 +378,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--method", default=os.environ.get("TCORR_BENCH_METHOD", "plain"))
+    ap.add_argument("--method", default=os.environ.get("TCORR_BENCH_METHOD", "fp16x3"))
+    ap.add_argument("--no-plain-compare", action="store_true")
     ap.add_argument("--workload", default="water", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -96,9 +96,11 @@ int run_corr(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
     const size_t need = align256(sizeof(double) * static_cast<size_t>(p.n_items) * p.WP);
     if (ws_bytes < need || (need > 0 && !d_ws)) return TCORR_EWORKSPACE;
     double *partial = static_cast<double *>(d_ws);
-    if (launch_plain_tiles(kind, d_x, p, partial, st) != cudaSuccess) return TCORR_ECUDA;
+    cudaError_t e = launch_plain_tiles(kind, d_x, p, partial, st);
+    if (e != cudaSuccess) return cuda_fail(e, "plain_tile_kernel launch");
     FinalizeArgs fa{0, nullptr, 0};
-    if (launch_lag_reduce(p, partial, fa, d_out, st) != cudaSuccess) return TCORR_ECUDA;
+    e = launch_lag_reduce(p, partial, fa, d_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
     return TCORR_OK;
 }
 

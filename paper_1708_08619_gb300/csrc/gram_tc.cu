@@ -1,19 +1,870 @@
-// Tensor-core banded Gram path (tcgen05).  Placeholder until the kernel lands:
-// every tensor-core method reports TCORR_EUNSUPPORTED.
+// Tensor-core banded Gram path (tcgen05, TMA, TMEM) for sm_103a.
+//
+// The origin x lag sum of Algorithms 9 and 11 is recast as a banded Gram
+// product.  With x_t the row of frame t (K = 3N values):
+//   ACF:  sum_{t0} x_{t0} . x_{t0+tau}                            = D(tau)
+//   MSD:  sum_{t0} |x_{t0+tau} - x_{t0}|^2 = P(tau) + Q(tau) - 2 D(tau)
+// where D(tau) sums the Gram entries G(t0, t0+tau) = x_{t0} . x_{t0+tau}
+// along one band offset, P(tau) = sum_{t0} S(t0), Q(tau) = sum_{t0} S(t0+tau)
+// and S(t) = |x_t|^2 (expanding |a - b|^2 = |a|^2 + |b|^2 - 2 a.b).  For the
+// MSD the positions are first referenced to frame 0 (x_t = r_t - r_0; the MSD
+// only sees differences) so that S and G stay small.
+//
+// Split precision: each FP32 value is written as x = hi + lo with hi and lo in
+// a 16-bit (or TF32) format and G is accumulated from hi.hi + hi.lo + lo.hi
+// (x3; x4 adds lo.lo) in FP32 in tensor memory.  FP16 operands carry a
+// per-frame power-of-two scale (so |x| <= 2^14 and hi, lo stay normal);
+// BF16 and TF32 need none.  S(t) is formed from the FP32 values in FP64.
+//
+// Kernels, in launch order:
+//   split_kernel      one block per frame: reference, scale, split, S(t)
+//   s_prefix_kernel   per-residue FP64 prefix sums of S (MSD only)
+//   gram_band_kernel  persistent, warp-specialised band tiles (below)
+//   lag_reduce        (reduce.cu) fixed-order FP64 reduction + MSD assembly
+//
+// gram_band_kernel: one CTA per SM, 10 warps.
+//   warp 0     TMA producer: per K-block loads A_hi, A_lo (128 origin rows)
+//              and B_hi, B_lo (192 frame rows) into a 5-stage smem ring
+//              (64-byte rows, 64B swizzle).
+//   warp 1     allocates TMEM (two 128 x 192 FP32 accumulators)
+//              and, from one lane, issues the tcgen05.mma chain.  The chain
+//              of a work item is cut into short sub-chains (sub_kb K-blocks,
+//              12 MMAs for x3) that alternate between the two accumulators:
+//              the tensor core's FP32 accumulation loses low bits on every
+//              accumulate step, so a long chain drifts low; short chains keep
+//              that loss small.
+//   warps 2-9  epilogue: two warps per TMEM lane quadrant, 96 columns each.
+//              Each sub-chain's accumulator is read with tcgen05.ld and added
+//              (FP32, round to nearest) into a per-thread register copy of
+//              its 128 entries; at the end of the item the band mask, the
+//              per-frame unscale and the diagonal sums (band offset
+//              w = j - i + 127) go to per-warp shared buffers, and a
+//              fixed-order combine writes one FP64 window per work item.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "tcorr_internal.cuh"
 
 namespace tcorr {
 
-__device__ unsigned int g_status;   // device status word (TCORR_OK or an error)
+__device__ unsigned int g_status;   // device status word (TCORR_OK or an error code)
 
-size_t gram_workspace_size(int64_t, int64_t, int64_t, int64_t, int) { return 0; }
+namespace {
 
-int gram_run(int, const float *, int64_t, int64_t, int64_t, int64_t, int, double *, void *, size_t,
-             cudaStream_t) {
-    return TCORR_EUNSUPPORTED;
+constexpr int BO = 128;             // origins per tile (MMA M)
+constexpr int BF = 192;             // frames per tile (MMA N)
+constexpr int STAGES = 5;
+constexpr int ROWB = 64;            // bytes of K per staged row = one 64B swizzle span
+constexpr int A_BYTES = BO * ROWB;  // 8 KB
+constexpr int B_BYTES = BF * ROWB;  // 12 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int WPG = 320;            // window width per item (>= BO + BF - 1 = 319)
+constexpr int NTHREADS = 320;   // 10 warps
+constexpr int NEPI = 8;          // epilogue warps
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int64_t kGramKseg = 4096; // K elements per work item (default)
+constexpr int kSubKb = 3;           // K-blocks per TMEM accumulation sub-chain (default)
+
+// Tuning knobs: TCORR_KSEG (K elements per work item, a multiple of 64) and
+// TCORR_SUB_KB (K-blocks per accumulation sub-chain, 1..8).  Longer
+// sub-chains trade accuracy for fewer accumulator hand-offs.
+int64_t gram_kseg() {
+    const char *e = std::getenv("TCORR_KSEG");
+    const long long v = e ? std::atoll(e) : 0;
+    return (v >= 64 && v % 64 == 0 && v <= (1 << 20)) ? v : kGramKseg;
+}
+int gram_sub_kb() {
+    const char *e = std::getenv("TCORR_SUB_KB");
+    const int v = e ? std::atoi(e) : 0;
+    return (v >= 1 && v <= 8) ? v : kSubKb;
+}
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+constexpr size_t SMEM_STAGES = size_t(STAGES) * STAGE_BYTES;
+constexpr size_t SMEM_LAG = NEPI * WPG * sizeof(float);
+constexpr size_t SMEM_CS = BF * sizeof(float);
+constexpr size_t SMEM_BAR = 16 * 8;
+constexpr size_t SMEM_TOTAL = 1024 + SMEM_STAGES + SMEM_LAG + SMEM_CS + SMEM_BAR + 16;
+
+enum Prec { P_FP16 = 0, P_BF16 = 1, P_TF32 = 2 };
+
+struct GramArgs {
+    int64_t T, s, tau_max, n_orig, n_res, n_rows, n_cols, n_items;
+    int64_t kb_total;       // K-blocks that hold data: ceil(K / BKe)
+    int64_t kb_per_item;    // K-blocks per work item
+    const float *inv_scale; // per-frame 2^-e (FP16), or nullptr
+    double *partial;        // [n_items][WPG]
+    int b3d;                // B map is 3-D (K, residue, frame index) when s > 1
+    int sub_kb;             // K-blocks per accumulation sub-chain
+};
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if it gave up (status word set) or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag) return false;
+            const unsigned long long now = globaltimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitNs) {
+                atomicExch(&g_status, static_cast<unsigned int>(TCORR_ETIMEOUT));
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int32_t c0,
+                                            int32_t c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int32_t c0,
+                                            int32_t c1, int32_t c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+template <int PREC>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (PREC == P_TF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+// 32 lanes x 32 columns of FP32 from TMEM, waited on before returning.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+// Two 32-column loads in flight, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, "
+        "%43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, "
+        "%62, %63}, [%65];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]),
+          "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]),
+          "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]),
+          "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]),
+          "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-bool gram_method_available(int) { return false; }
+// Shared-memory matrix descriptor for a K-major tile with 64-byte rows and the
+// 64B swizzle: 8-row groups are 512 bytes apart (stride byte offset), the
+// leading byte offset is unused for this layout, version field = 1.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(1u) << 16;                  // leading byte offset (unused)
+    d |= static_cast<uint64_t>((512u >> 4) & 0x3FFFu) << 32; // stride byte offset
+    d |= static_cast<uint64_t>(1u) << 46;                  // descriptor version
+    d |= static_cast<uint64_t>(4u) << 61;                  // 64B swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B K-major, M = 128, N = 256.
+template <int PREC>
+__host__ __device__ constexpr uint32_t make_idesc() {
+    return (1u << 4)                                                       // D format F32
+           | ((PREC == P_FP16 ? 0u : PREC == P_BF16 ? 1u : 2u) << 7)       // A format
+           | ((PREC == P_FP16 ? 0u : PREC == P_BF16 ? 1u : 2u) << 10)      // B format
+           | (static_cast<uint32_t>(BF >> 3) << 17)                        // N >> 3
+           | (static_cast<uint32_t>(BO >> 4) << 24);                       // M >> 4
+}
+
+struct Item {
+    int64_t rho, r, c, o0, k0, m_max, kb0, kb1;
+    bool empty;
+};
+
+__device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
+    Item I;
+    int64_t t = item;
+    I.c = t % a.n_cols;
+    t /= a.n_cols;
+    I.r = t % a.n_rows;
+    t /= a.n_rows;
+    I.rho = t % a.n_res;
+    const int64_t g = t / a.n_res;
+    I.o0 = I.r * BO;
+    I.k0 = I.o0 + I.c * BF;
+    I.m_max = (a.tau_max - I.rho) / a.s;
+    const int64_t n_rho = n_frames_res(a.T, a.s, I.rho);
+    I.kb0 = g * a.kb_per_item;
+    I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
+    I.empty = (I.c * BF - BO + 1 > I.m_max) || (I.k0 >= n_rho) || (I.kb0 >= I.kb1);
+    return I;
+}
+
+// 10 warps: three share one SM sub-partition's 16K registers, so at most
+// 168 registers per thread (the epilogue keeps 96 FP32 accumulators).
+template <int PREC, bool X4>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_band_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                     GramArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *stages = smem;
+    float *lagbuf = reinterpret_cast<float *>(smem + SMEM_STAGES);            // [NEPI][WPG]
+    float *cs = reinterpret_cast<float *>(smem + SMEM_STAGES + SMEM_LAG);     // [BF]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SMEM_STAGES + SMEM_LAG + SMEM_CS);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int st) { return bar0 + 8u * st; };
+    auto empty_bar = [&](int st) { return bar0 + 8u * (STAGES + st); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(full_bar(st), 1);
+            mbar_init(empty_bar(st), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), NEPI);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp >= 2) {
+        for (int i = threadIdx.x - 64; i < NEPI * WPG; i += 32 * NEPI) lagbuf[i] = 0.f;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int64_t sub_kb = a.sub_kb;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        int st = 0;
+        uint32_t ph = 0;
+        for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+            const Item I = decode_item(a, item);
+            if (I.empty) continue;
+            for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
+                if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
+                mbar_arrive_expect_tx(full_bar(st), STAGE_BYTES);
+                const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
+                const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
+                tma_load_2d(sbase, &tmAh, kx, static_cast<int32_t>(I.o0), full_bar(st));
+                tma_load_2d(sbase + A_BYTES, &tmAl, kx, static_cast<int32_t>(I.o0), full_bar(st));
+                if (a.b3d) {
+                    tma_load_3d(sbase + 2 * A_BYTES, &tmBh, kx, static_cast<int32_t>(I.rho),
+                                static_cast<int32_t>(I.k0), full_bar(st));
+                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, &tmBl, kx, static_cast<int32_t>(I.rho),
+                                static_cast<int32_t>(I.k0), full_bar(st));
+                } else {
+                    tma_load_2d(sbase + 2 * A_BYTES, &tmBh, kx, static_cast<int32_t>(I.k0), full_bar(st));
+                    tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, &tmBl, kx, static_cast<int32_t>(I.k0),
+                                full_bar(st));
+                }
+                if (++st == STAGES) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+    producer_done:;
+    } else if (warp == 1 && lane == 0) {
+        // --------------------------------------------------------------- MMA
+        constexpr uint32_t idesc = make_idesc<PREC>();
+        int st = 0;
+        uint32_t ph = 0, chain = 0;
+        bool issued = false, aborted = false;
+        for (int64_t item = blockIdx.x; item < a.n_items && !aborted; item += gridDim.x) {
+            const Item I = decode_item(a, item);
+            if (I.empty) continue;
+            for (int64_t kc = I.kb0; kc < I.kb1 && !aborted; kc += sub_kb) {
+                const int64_t kc1 = min(I.kb1, kc + sub_kb);
+                const int b = chain & 1;
+                if (!mbar_wait(tempty_bar(b), ((chain >> 1) & 1u) ^ 1u, abort_flag)) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + static_cast<uint32_t>(b * BF);
+                for (int64_t kb = kc; kb < kc1; ++kb) {
+                    if (!mbar_wait(full_bar(st), ph, abort_flag)) {
+                        aborted = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sA = smem_u32(stages + size_t(st) * STAGE_BYTES);
+                    const uint64_t dAh = smem_desc_sw64(sA);
+                    const uint64_t dAl = smem_desc_sw64(sA + A_BYTES);
+                    const uint64_t dBh = smem_desc_sw64(sA + 2 * A_BYTES);
+                    const uint64_t dBl = smem_desc_sw64(sA + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t adv = static_cast<uint64_t>(ks * 2);   // 32 bytes of K in 16-byte units
+                        const uint32_t acc = (kb != kc || ks != 0) ? 1u : 0u;
+                        tc_mma<PREC>(d, dAh + adv, dBh + adv, idesc, acc);
+                        tc_mma<PREC>(d, dAh + adv, dBl + adv, idesc, 1u);
+                        tc_mma<PREC>(d, dAl + adv, dBh + adv, idesc, 1u);
+                        if (X4) tc_mma<PREC>(d, dAl + adv, dBl + adv, idesc, 1u);
+                    }
+                    issued = true;
+                    tc_commit(empty_bar(st));
+                    if (++st == STAGES) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (aborted) break;
+                tc_commit(tfull_bar(b));
+                ++chain;
+            }
+        }
+        if (issued) {   // wait (bounded) until every MMA this thread issued has completed
+            tc_commit(drain_bar);
+            int dummy = 0;
+            volatile int *never = &dummy;
+            mbar_wait(drain_bar, 0u, never);
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;     // which 96 accumulator columns
+        const int row = 32 * q + lane;        // accumulator row = origin o0 + row
+        const int et = threadIdx.x - 64;      // 0 .. 32*NEPI-1
+        float *lb = lagbuf + (warp - 2) * WPG;
+        uint32_t chain = 0;
+        bool aborted = false;
+        for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+            const Item I = decode_item(a, item);
+            double *outp = a.partial + item * WPG;
+            if (I.empty) {
+                for (int w = et; w < WPG; w += 32 * NEPI) outp[w] = 0.0;
+                continue;
+            }
+            float acc2[BF / 2];
+#pragma unroll
+            for (int j = 0; j < BF / 2; ++j) acc2[j] = 0.f;
+            for (int64_t kc = I.kb0; kc < I.kb1; kc += sub_kb) {
+                const int b = chain & 1;
+                if (!mbar_wait(tfull_bar(b), (chain >> 1) & 1u, abort_flag)) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + (static_cast<uint32_t>(32 * q) << 16) +
+                                       static_cast<uint32_t>(b * BF + (BF / 2) * half);
+                {
+                    uint32_t v[64];
+                    tmem_ld64(tbase, v);
+#pragma unroll
+                    for (int jj = 0; jj < 64; ++jj) acc2[jj] += __uint_as_float(v[jj]);
+                }
+                {
+                    uint32_t v[32];
+                    tmem_ld32(tbase + 64, v);
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) acc2[64 + jj] += __uint_as_float(v[jj]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty_bar(b));
+                ++chain;
+            }
+            if (aborted) break;
+            float rs = 1.f;
+            if (PREC == P_FP16) {
+                for (int j = et; j < BF; j += 32 * NEPI) {
+                    const int64_t f = I.rho + (I.k0 + j) * a.s;
+                    cs[j] = f < a.T ? a.inv_scale[f] : 1.f;
+                }
+                rs = (I.o0 + row < a.n_orig) ? a.inv_scale[(I.o0 + row) * a.s] : 1.f;
+                named_bar_sync(1, 32 * NEPI);
+            }
+            const int64_t mrow = I.c * BF - row;      // band offset m = mrow + j
+#pragma unroll
+            for (int jj = 0; jj < BF / 2; ++jj) {
+                const int j = (BF / 2) * half + jj;
+                const int64_t m = mrow + j;
+                if (m >= 0 && m <= I.m_max) {
+                    float val = acc2[jj];
+                    if (PREC == P_FP16) val = (val * rs) * cs[j];
+                    atomicAdd(&lb[j - row + (BO - 1)], val);
+                }
+            }
+            named_bar_sync(1, 32 * NEPI);
+            for (int w = et; w < WPG; w += 32 * NEPI) {
+                float sum = 0.f;
+#pragma unroll
+                for (int e = 0; e < NEPI; ++e) {
+                    sum += lagbuf[e * WPG + w];
+                    lagbuf[e * WPG + w] = 0.f;
+                }
+                outp[w] = static_cast<double>(sum);
+            }
+            named_bar_sync(1, 32 * NEPI);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ prep
+// One block per padded frame row t.  x = X[t] - X[0] (MSD) or X[t] (ACF);
+// FP16 rows are scaled by 2^e_t with e_t chosen so max |x| * 2^e_t < 2^14.
+constexpr int PREP_THREADS = 256;
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+template <int PREC, int KIND>
+__global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__restrict__ X, int64_t T,
+                                                             int64_t K, int64_t Kp, void *Xh, void *Xl,
+                                                             float *inv_scale, double *S) {
+    __shared__ float red_f[PREP_THREADS / 32];
+    __shared__ double red_d[PREP_THREADS];
+    const int64_t t = blockIdx.x;
+    const int tid = threadIdx.x;
+    const bool live = t < T;
+    const float *row = X + t * K;
+    auto value = [&](int64_t k) -> float {
+        if (!live || k >= K) return 0.f;
+        return KIND == 0 ? row[k] - X[k] : row[k];
+    };
+    float scale = 1.f;
+    if (PREC == P_FP16) {
+        float mx = 0.f;
+        for (int64_t k = tid; k < K && live; k += PREP_THREADS) mx = fmaxf(mx, fabsf(value(k)));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if ((tid & 31) == 0) red_f[tid >> 5] = mx;
+        __syncthreads();
+        mx = red_f[0];
+        for (int i = 1; i < PREP_THREADS / 32; ++i) mx = fmaxf(mx, red_f[i]);
+        int e = 0;
+        if (mx > 0.f) {
+            int ex;
+            frexpf(mx, &ex);          // mx < 2^ex
+            e = 14 - ex;
+            e = e < -60 ? -60 : (e > 60 ? 60 : e);
+        }
+        scale = ldexpf(1.f, e);
+        if (tid == 0) inv_scale[t] = ldexpf(1.f, -e);
+    }
+    double sacc = 0.0;
+    for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < Kp; k0 += PREP_THREADS * 8) {
+        float x[8];
+        float sq = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            x[i] = value(k0 + i);
+            sq = fmaf(x[i], x[i], sq);
+        }
+        sacc += static_cast<double>(sq);
+        if (PREC == P_TF32) {
+            uint32_t h[8], l[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                h[i] = tf32_rna(x[i]);
+                l[i] = tf32_rna(x[i] - __uint_as_float(h[i]));
+            }
+            uint4 *ph = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xh) + t * Kp + k0);
+            uint4 *pl = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xl) + t * Kp + k0);
+            ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
+            ph[1] = make_uint4(h[4], h[5], h[6], h[7]);
+            pl[0] = make_uint4(l[0], l[1], l[2], l[3]);
+            pl[1] = make_uint4(l[4], l[5], l[6], l[7]);
+        } else {
+            uint16_t h[8], l[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (PREC == P_FP16) {
+                    const float xs = x[i] * scale;
+                    const __half hh = __float2half_rn(xs);
+                    const __half ll = __float2half_rn(xs - __half2float(hh));
+                    h[i] = __half_as_ushort(hh);
+                    l[i] = __half_as_ushort(ll);
+                } else {
+                    const __nv_bfloat16 hh = __float2bfloat16_rn(x[i]);
+                    const __nv_bfloat16 ll = __float2bfloat16_rn(x[i] - __bfloat162float(hh));
+                    h[i] = __bfloat16_as_ushort(hh);
+                    l[i] = __bfloat16_as_ushort(ll);
+                }
+            }
+            uint4 vh, vl;
+            vh.x = h[0] | (uint32_t(h[1]) << 16);
+            vh.y = h[2] | (uint32_t(h[3]) << 16);
+            vh.z = h[4] | (uint32_t(h[5]) << 16);
+            vh.w = h[6] | (uint32_t(h[7]) << 16);
+            vl.x = l[0] | (uint32_t(l[1]) << 16);
+            vl.y = l[2] | (uint32_t(l[3]) << 16);
+            vl.z = l[4] | (uint32_t(l[5]) << 16);
+            vl.w = l[6] | (uint32_t(l[7]) << 16);
+            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xh) + t * Kp + k0) = vh;
+            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xl) + t * Kp + k0) = vl;
+        }
+    }
+    if (KIND == 0 && S != nullptr) {
+        red_d[tid] = sacc;
+        __syncthreads();
+        for (int off = PREP_THREADS / 2; off > 0; off >>= 1) {
+            if (tid < off) red_d[tid] += red_d[tid + off];
+            __syncthreads();
+        }
+        if (tid == 0 && live) S[t] = red_d[0];
+    }
+}
+
+// prefix[rho][j] = sum_{j' < j} S(rho + j' s), j = 0 .. n_rho.  One block per
+// residue; contiguous chunks per thread, chunk totals scanned in order.
+constexpr int PFX_THREADS = 1024;
+
+__global__ void s_prefix_kernel(const double *S, int64_t T, int64_t s, int64_t pstride, double *prefix) {
+    __shared__ double tot[PFX_THREADS];
+    const int64_t rho = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int64_t n = n_frames_res(T, s, rho);
+    double *pr = prefix + rho * pstride;
+    const int64_t per = ceil_div(n > 0 ? n : 1, PFX_THREADS);
+    const int64_t b = tid * per, e = min(n, b + per);
+    double acc = 0.0;
+    for (int64_t j = b; j < e; ++j) acc += S[rho + j * s];
+    tot[tid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double run = 0.0;
+        for (int i = 0; i < PFX_THREADS; ++i) {
+            const double v = tot[i];
+            tot[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    double run = tot[tid];
+    if (tid == 0) pr[0] = 0.0;
+    for (int64_t j = b; j < e; ++j) {
+        run += S[rho + j * s];
+        pr[j + 1] = run;
+    }
+}
+
+// ------------------------------------------------------------------ host
+struct GramLayout {
+    BandPlan p;
+    int prec;
+    bool x4;
+    int64_t Kp, T_pad, n_k, esize, bke, pstride, kseg;
+    size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, total;
+};
+
+bool method_prec(int method, int *prec, bool *x4) {
+    switch (method) {
+        case TCORR_TC_FP16X3: *prec = P_FP16; *x4 = false; return true;
+        case TCORR_TC_BF16X3: *prec = P_BF16; *x4 = false; return true;
+        case TCORR_TC_BF16X4: *prec = P_BF16; *x4 = true; return true;
+        case TCORR_TC_TF32X3: *prec = P_TF32; *x4 = false; return true;
+        default: return false;
+    }
+}
+
+bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int kind, GramLayout *L) {
+    if (!method_prec(method, &L->prec, &L->x4)) return false;
+    L->esize = L->prec == P_TF32 ? 4 : 2;
+    L->bke = L->prec == P_TF32 ? 16 : 32;
+    const int64_t K = 3 * N;
+    L->Kp = ceil_div(K, 64) * 64;
+    L->n_k = ceil_div(T, s);
+    L->T_pad = L->n_k * s;           // rows rho + k s for every rho < s, k < n_k exist
+    L->kseg = gram_kseg();
+    L->p = make_band_plan(T, N, tau_max, s, BO, BF, L->kseg, 1);
+    L->p.WP = WPG;
+    // one K group per segment of kseg elements
+    const int64_t kb_total = ceil_div(K, L->bke);
+    const int64_t kb_per_item = L->kseg / L->bke;
+    L->p.n_groups = ceil_div(kb_total, kb_per_item);
+    L->p.segs_per_item = 1;
+    L->p.n_items = L->p.n_groups * L->p.n_res * L->p.n_rows * L->p.n_cols;
+    L->pstride = (T - 1) / s + 2;
+    // TMA coordinates are 32-bit
+    if (L->Kp >= (int64_t(1) << 31) || L->T_pad >= (int64_t(1) << 31)) return false;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L->off_xh = take(size_t(L->T_pad) * L->Kp * L->esize);
+    L->off_xl = take(size_t(L->T_pad) * L->Kp * L->esize);
+    L->off_scale = take(size_t(L->T_pad) * sizeof(float));
+    L->off_S = take(kind == 0 ? size_t(T) * sizeof(double) : 0);
+    L->off_prefix = take(kind == 0 ? size_t(L->p.n_res) * L->pstride * sizeof(double) : 0);
+    L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
+    L->total = off;
+    return true;
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+bool device_is_sm103(int *num_sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    return major == 10 && minor == 3;
+}
+
+template <int PREC, bool X4>
+cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(gram_band_kernel<PREC, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(SMEM_TOTAL));
+    if (e != cudaSuccess) return e;
+    gram_band_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(maps[0], maps[1], maps[2], maps[3], ga);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_split(int kind, const float *X, const GramLayout &L, uint8_t *ws, cudaStream_t st) {
+    void *xh = ws + L.off_xh, *xl = ws + L.off_xl;
+    float *sc = reinterpret_cast<float *>(ws + L.off_scale);
+    double *S = kind == 0 ? reinterpret_cast<double *>(ws + L.off_S) : nullptr;
+    const int64_t K = L.p.K;
+    if (kind == 0)
+        split_kernel<PREC, 0><<<static_cast<unsigned>(L.T_pad), PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+    else
+        split_kernel<PREC, 1><<<static_cast<unsigned>(L.T_pad), PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method) {
+    GramLayout L;
+    if (!make_layout(T, N, tau_max, s, method, 0, &L)) return 0;
+    return L.total;
+}
+
+bool gram_method_available(int method) {
+    int prec;
+    bool x4;
+    int sms = 0;
+    return method_prec(method, &prec, &x4) && device_is_sm103(&sms) && get_encode() != nullptr;
+}
+
+int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+    GramLayout L;
+    if (!make_layout(T, N, tau_max, s, method, kind, &L)) return TCORR_EUNSUPPORTED;
+    GramLayout Lmax;
+    make_layout(T, N, tau_max, s, method, 0, &Lmax);
+    if (ws_bytes < Lmax.total || !d_ws) return TCORR_EWORKSPACE;
+    int num_sms = 0;
+    if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
+    EncodeFn encode = get_encode();
+    if (!encode) return TCORR_EUNSUPPORTED;
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+
+    cudaError_t e = cudaSuccess;
+    switch (L.prec) {
+        case P_FP16: e = launch_split<P_FP16>(kind, d_x, L, ws, st); break;
+        case P_BF16: e = launch_split<P_BF16>(kind, d_x, L, ws, st); break;
+        default: e = launch_split<P_TF32>(kind, d_x, L, ws, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "split_kernel launch");
+    if (kind == 0) {
+        s_prefix_kernel<<<static_cast<unsigned>(L.p.n_res), PFX_THREADS, 0, st>>>(
+            reinterpret_cast<double *>(ws + L.off_S), T, s, L.pstride, reinterpret_cast<double *>(ws + L.off_prefix));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "s_prefix_kernel launch");
+    }
+
+    // Tensor maps: A rows are origins o (frame o s); B rows are frames rho + k s.
+    const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUtensorMap maps[4];
+    void *bases[2] = {ws + L.off_xh, ws + L.off_xl};
+    const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kp * L.esize);
+    for (int h = 0; h < 2; ++h) {
+        const cuuint64_t dimA[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.p.n_orig)};
+        const cuuint64_t strA[1] = {rowb * static_cast<cuuint64_t>(s)};
+        const cuuint32_t boxA[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BO)};
+        const cuuint32_t es2[2] = {1, 1};
+            if (encode(&maps[h], dt, 2, bases[h], dimA, strA, boxA, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+        CUresult rb;
+        if (s > 1) {
+            const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(s),
+                                        static_cast<cuuint64_t>(L.n_k)};
+            const cuuint64_t strB[2] = {rowb, rowb * static_cast<cuuint64_t>(s)};
+            const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), 1, static_cast<cuuint32_t>(BF)};
+            const cuuint32_t es3[3] = {1, 1, 1};
+            rb = encode(&maps[2 + h], dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            const cuuint64_t dimB[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.n_k)};
+            const cuuint64_t strB[1] = {rowb};
+            const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BF)};
+            rb = encode(&maps[2 + h], dt, 2, bases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
+        if (rb != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+    }
+
+    GramArgs ga;
+    ga.T = T;
+    ga.s = s;
+    ga.tau_max = tau_max;
+    ga.n_orig = L.p.n_orig;
+    ga.n_res = L.p.n_res;
+    ga.n_rows = L.p.n_rows;
+    ga.n_cols = L.p.n_cols;
+    ga.n_items = L.p.n_items;
+    ga.kb_total = ceil_div(3 * N, L.bke);
+    ga.kb_per_item = L.kseg / L.bke;
+    ga.inv_scale = reinterpret_cast<const float *>(ws + L.off_scale);
+    ga.partial = reinterpret_cast<double *>(ws + L.off_partial);
+    ga.b3d = s > 1 ? 1 : 0;
+    ga.sub_kb = gram_sub_kb();
+    const int grid = static_cast<int>(L.p.n_items < num_sms ? L.p.n_items : num_sms);
+    switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st); break;
+        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
+
+    FinalizeArgs fa{kind == 0 ? 1 : 0, kind == 0 ? reinterpret_cast<const double *>(ws + L.off_prefix) : nullptr,
+                    L.pstride};
+    e = launch_lag_reduce(L.p, ga.partial, fa, d_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
+    return TCORR_OK;
+}
 
 int status_poll_and_clear(cudaStream_t st) {
     if (cudaStreamSynchronize(st) != cudaSuccess) return TCORR_ECUDA;

@@ -19,6 +19,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include "../../include/tcorr.h"
@@ -56,6 +58,13 @@ __host__ __device__ inline int64_t n_frames_res(int64_t T, int64_t s, int64_t rh
 // that the grid has enough blocks to fill the GPU.
 BandPlan make_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int BO, int BF,
                         int64_t kseg, int64_t min_items);
+
+// Maps a failed CUDA call to TCORR_ECUDA; with TCORR_VERBOSE set in the
+// environment it also prints the call site and CUDA's error string.
+inline int cuda_fail(cudaError_t e, const char *what) {
+    if (std::getenv("TCORR_VERBOSE")) std::fprintf(stderr, "tcorr: %s: %s\n", what, cudaGetErrorString(e));
+    return TCORR_ECUDA;
+}
 
 // Workspace layout helpers (byte offsets, 256-byte aligned).
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }

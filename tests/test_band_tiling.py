@@ -28,7 +28,7 @@ def plan(T, tau_max, s, BO, BF):
 
 @pytest.mark.parametrize("T,tau_max,s,BO,BF", [
     (1, 0, 1, 4, 4), (10, 9, 1, 4, 4), (10, 3, 1, 4, 8), (17, 16, 3, 4, 4), (30, 12, 5, 4, 8),
-    (40, 39, 7, 8, 4), (23, 5, 30, 4, 4), (64, 63, 64, 8, 8), (50, 20, 2, 8, 16),
+    (40, 39, 7, 8, 4), (23, 5, 30, 4, 4), (64, 63, 64, 8, 8), (50, 20, 2, 8, 16), (70, 40, 1, 8, 12), (45, 30, 4, 4, 6),
 ])
 def test_band_tiles_cover_each_pair_once(T, tau_max, s, BO, BF):
     p = plan(T, tau_max, s, BO, BF)
