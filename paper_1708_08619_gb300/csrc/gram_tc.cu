@@ -518,29 +518,104 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
-template <int PREC, int KIND>
+template <int PREC>
+__device__ __forceinline__ void split_store8(const float (&x)[8], float scale, void *Xh, void *Xl, int64_t off) {
+    if (PREC == P_TF32) {
+        uint32_t h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            h[i] = tf32_rna(x[i]);
+            l[i] = tf32_rna(x[i] - __uint_as_float(h[i]));
+        }
+        uint4 *ph = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xh) + off);
+        uint4 *pl = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xl) + off);
+        ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        ph[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        pl[0] = make_uint4(l[0], l[1], l[2], l[3]);
+        pl[1] = make_uint4(l[4], l[5], l[6], l[7]);
+    } else {
+        uint16_t h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (PREC == P_FP16) {
+                const float xs = x[i] * scale;
+                const __half hh = __float2half_rn(xs);
+                const __half ll = __float2half_rn(xs - __half2float(hh));
+                h[i] = __half_as_ushort(hh);
+                l[i] = __half_as_ushort(ll);
+            } else {
+                const __nv_bfloat16 hh = __float2bfloat16_rn(x[i]);
+                const __nv_bfloat16 ll = __float2bfloat16_rn(x[i] - __bfloat162float(hh));
+                h[i] = __bfloat16_as_ushort(hh);
+                l[i] = __bfloat16_as_ushort(ll);
+            }
+        }
+        uint4 vh, vl;
+        vh.x = h[0] | (uint32_t(h[1]) << 16);
+        vh.y = h[2] | (uint32_t(h[3]) << 16);
+        vh.z = h[4] | (uint32_t(h[5]) << 16);
+        vh.w = h[6] | (uint32_t(h[7]) << 16);
+        vl.x = l[0] | (uint32_t(l[1]) << 16);
+        vl.y = l[2] | (uint32_t(l[3]) << 16);
+        vl.z = l[4] | (uint32_t(l[5]) << 16);
+        vl.w = l[6] | (uint32_t(l[7]) << 16);
+        *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xh) + off) = vh;
+        *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xl) + off) = vl;
+    }
+}
+
+// Eight consecutive values x = X[t][k..k+7] (- X[0][k..k+7] for the MSD),
+// zero past K.  VEC: rows are 16-byte aligned and K % 4 == 0 (float4 loads).
+template <int KIND, bool VEC>
+__device__ __forceinline__ void load8(const float *__restrict__ row, const float *__restrict__ ref, int64_t k,
+                                      int64_t K, float (&x)[8]) {
+    if (VEC && k + 8 <= K) {
+        const float4 a0 = __ldg(reinterpret_cast<const float4 *>(row + k));
+        const float4 a1 = __ldg(reinterpret_cast<const float4 *>(row + k + 4));
+        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+        x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+        if (KIND == 0) {
+            const float4 r0 = __ldg(reinterpret_cast<const float4 *>(ref + k));
+            const float4 r1 = __ldg(reinterpret_cast<const float4 *>(ref + k + 4));
+            x[0] -= r0.x; x[1] -= r0.y; x[2] -= r0.z; x[3] -= r0.w;
+            x[4] -= r1.x; x[5] -= r1.y; x[6] -= r1.z; x[7] -= r1.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t kk = k + i;
+            x[i] = kk < K ? (KIND == 0 ? __ldg(row + kk) - __ldg(ref + kk) : __ldg(row + kk)) : 0.f;
+        }
+    }
+}
+
+template <int PREC, int KIND, bool VEC>
 __global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__restrict__ X, int64_t T,
                                                              int64_t K, int64_t Kp, void *Xh, void *Xl,
                                                              float *inv_scale, double *S) {
     __shared__ float red_f[PREP_THREADS / 32];
-    __shared__ double red_d[PREP_THREADS];
+    __shared__ double red_d[PREP_THREADS / 32];
     const int64_t t = blockIdx.x;
     const int tid = threadIdx.x;
     const bool live = t < T;
-    const float *row = X + t * K;
-    auto value = [&](int64_t k) -> float {
-        if (!live || k >= K) return 0.f;
-        return KIND == 0 ? row[k] - X[k] : row[k];
-    };
+    const float *row = X + (live ? t : 0) * K;
+    const int64_t Klive = live ? K : 0;      // padding rows are all zero
+    constexpr int64_t STEP = PREP_THREADS * 8;
     float scale = 1.f;
     if (PREC == P_FP16) {
         float mx = 0.f;
-        for (int64_t k = tid; k < K && live; k += PREP_THREADS) mx = fmaxf(mx, fabsf(value(k)));
+        for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < Klive; k0 += STEP) {
+            float x[8];
+            load8<KIND, VEC>(row, X, k0, Klive, x);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(x[i]));
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
         if ((tid & 31) == 0) red_f[tid >> 5] = mx;
         __syncthreads();
         mx = red_f[0];
+#pragma unroll
         for (int i = 1; i < PREP_THREADS / 32; ++i) mx = fmaxf(mx, red_f[i]);
         int e = 0;
         if (mx > 0.f) {
@@ -553,75 +628,63 @@ __global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__rest
         if (tid == 0) inv_scale[t] = ldexpf(1.f, -e);
     }
     double sacc = 0.0;
-    for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < Kp; k0 += PREP_THREADS * 8) {
+    for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < Kp; k0 += STEP) {
         float x[8];
-        float sq = 0.f;
+        load8<KIND, VEC>(row, X, k0, Klive, x);
+        if (KIND == 0) {
+            float sq = 0.f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            x[i] = value(k0 + i);
-            sq = fmaf(x[i], x[i], sq);
+            for (int i = 0; i < 8; ++i) sq = fmaf(x[i], x[i], sq);
+            sacc += static_cast<double>(sq);
         }
-        sacc += static_cast<double>(sq);
-        if (PREC == P_TF32) {
-            uint32_t h[8], l[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                h[i] = tf32_rna(x[i]);
-                l[i] = tf32_rna(x[i] - __uint_as_float(h[i]));
-            }
-            uint4 *ph = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xh) + t * Kp + k0);
-            uint4 *pl = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xl) + t * Kp + k0);
-            ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
-            ph[1] = make_uint4(h[4], h[5], h[6], h[7]);
-            pl[0] = make_uint4(l[0], l[1], l[2], l[3]);
-            pl[1] = make_uint4(l[4], l[5], l[6], l[7]);
-        } else {
-            uint16_t h[8], l[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (PREC == P_FP16) {
-                    const float xs = x[i] * scale;
-                    const __half hh = __float2half_rn(xs);
-                    const __half ll = __float2half_rn(xs - __half2float(hh));
-                    h[i] = __half_as_ushort(hh);
-                    l[i] = __half_as_ushort(ll);
-                } else {
-                    const __nv_bfloat16 hh = __float2bfloat16_rn(x[i]);
-                    const __nv_bfloat16 ll = __float2bfloat16_rn(x[i] - __bfloat162float(hh));
-                    h[i] = __bfloat16_as_ushort(hh);
-                    l[i] = __bfloat16_as_ushort(ll);
-                }
-            }
-            uint4 vh, vl;
-            vh.x = h[0] | (uint32_t(h[1]) << 16);
-            vh.y = h[2] | (uint32_t(h[3]) << 16);
-            vh.z = h[4] | (uint32_t(h[5]) << 16);
-            vh.w = h[6] | (uint32_t(h[7]) << 16);
-            vl.x = l[0] | (uint32_t(l[1]) << 16);
-            vl.y = l[2] | (uint32_t(l[3]) << 16);
-            vl.z = l[4] | (uint32_t(l[5]) << 16);
-            vl.w = l[6] | (uint32_t(l[7]) << 16);
-            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xh) + t * Kp + k0) = vh;
-            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xl) + t * Kp + k0) = vl;
-        }
+        split_store8<PREC>(x, scale, Xh, Xl, t * Kp + k0);
     }
     if (KIND == 0 && S != nullptr) {
-        red_d[tid] = sacc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+        if ((tid & 31) == 0) red_d[tid >> 5] = sacc;
         __syncthreads();
-        for (int off = PREP_THREADS / 2; off > 0; off >>= 1) {
-            if (tid < off) red_d[tid] += red_d[tid + off];
-            __syncthreads();
+        if (tid == 0 && live) {
+            double tot = 0.0;
+#pragma unroll
+            for (int i = 0; i < PREP_THREADS / 32; ++i) tot += red_d[i];
+            S[t] = tot;
         }
-        if (tid == 0 && live) S[t] = red_d[0];
     }
 }
 
 // prefix[rho][j] = sum_{j' < j} S(rho + j' s), j = 0 .. n_rho.  One block per
-// residue; contiguous chunks per thread, chunk totals scanned in order.
+// residue; each thread owns a contiguous chunk; chunk totals are scanned with
+// a fixed warp-shuffle tree, so the result does not depend on timing.
 constexpr int PFX_THREADS = 1024;
 
-__global__ void s_prefix_kernel(const double *S, int64_t T, int64_t s, int64_t pstride, double *prefix) {
-    __shared__ double tot[PFX_THREADS];
+__device__ __forceinline__ double block_exclusive_scan(double v, double *warp_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += u;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < (blockDim.x >> 5) ? warp_tot[lane] : 0.0;
+        double xi = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += u;
+        }
+        warp_tot[lane] = xi - x;     // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    return warp_tot[w] + (inc - v);
+}
+
+__global__ void __launch_bounds__(PFX_THREADS) s_prefix_kernel(const double *S, int64_t T, int64_t s,
+                                                                int64_t pstride, double *prefix) {
+    __shared__ double warp_tot[32];
     const int64_t rho = blockIdx.x;
     const int tid = threadIdx.x;
     const int64_t n = n_frames_res(T, s, rho);
@@ -630,18 +693,7 @@ __global__ void s_prefix_kernel(const double *S, int64_t T, int64_t s, int64_t p
     const int64_t b = tid * per, e = min(n, b + per);
     double acc = 0.0;
     for (int64_t j = b; j < e; ++j) acc += S[rho + j * s];
-    tot[tid] = acc;
-    __syncthreads();
-    if (tid == 0) {
-        double run = 0.0;
-        for (int i = 0; i < PFX_THREADS; ++i) {
-            const double v = tot[i];
-            tot[i] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    double run = tot[tid];
+    double run = block_exclusive_scan(acc, warp_tot);
     if (tid == 0) pr[0] = 0.0;
     for (int64_t j = b; j < e; ++j) {
         run += S[rho + j * s];
@@ -749,10 +801,15 @@ cudaError_t launch_split(int kind, const float *X, const GramLayout &L, uint8_t 
     float *sc = reinterpret_cast<float *>(ws + L.off_scale);
     double *S = kind == 0 ? reinterpret_cast<double *>(ws + L.off_S) : nullptr;
     const int64_t K = L.p.K;
-    if (kind == 0)
-        split_kernel<PREC, 0><<<static_cast<unsigned>(L.T_pad), PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
-    else
-        split_kernel<PREC, 1><<<static_cast<unsigned>(L.T_pad), PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+    const bool vec = (K % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+    const unsigned g = static_cast<unsigned>(L.T_pad);
+    if (kind == 0) {
+        if (vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+        else split_kernel<PREC, 0, false><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+    } else {
+        if (vec) split_kernel<PREC, 1, true><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+        else split_kernel<PREC, 1, false><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+    }
     return cudaGetLastError();
 }
 

@@ -73,33 +73,41 @@ __global__ void lag_reduce_kernel(ReduceArgs a) {
     }
 }
 
-// Running trapezoid.  One block: thread t owns a contiguous chunk, forms its
-// local running sum, the chunk totals are scanned by thread 0 in order, then
-// each thread adds its offset.  Fixed order throughout.
+// Running trapezoid.  One block: thread t owns a contiguous chunk of the
+// increments dt (c[k-1] + c[k]) / 2, the chunk totals are combined by a fixed
+// warp-shuffle scan, then each thread writes its running values.
 constexpr int GK_THREADS = 1024;
 
-__global__ void gk_integrate_kernel(const double *c, int64_t n, double dt, double prefactor,
-                                    double *running) {
-    __shared__ double tot[GK_THREADS];
-    const int t = threadIdx.x;
+__global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *c, int64_t n, double dt,
+                                                                   double prefactor, double *running) {
+    __shared__ double warp_tot[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t nseg = n - 1;                     // increments k = 1 .. n-1
     const int64_t per = ceil_div(nseg > 0 ? nseg : 1, GK_THREADS);
     const int64_t b = 1 + t * per;
     const int64_t e = min(n, b + per);
     double acc = 0.0;
     for (int64_t k = b; k < e; ++k) acc += dt * (c[k - 1] + c[k]) / 2.0;
-    tot[t] = acc;
+    double inc = acc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += u;
+    }
+    if (lane == 31) warp_tot[w] = inc;
     __syncthreads();
-    if (t == 0) {
-        double run = 0.0;
-        for (int i = 0; i < GK_THREADS; ++i) {
-            const double v = tot[i];
-            tot[i] = run;
-            run += v;
+    if (w == 0) {
+        const double x = warp_tot[lane];
+        double xi = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += u;
         }
+        warp_tot[lane] = xi - x;
     }
     __syncthreads();
-    double I = tot[t];
+    double I = warp_tot[w] + (inc - acc);
     if (t == 0) running[0] = 0.0;
     for (int64_t k = b; k < e; ++k) {
         I += dt * (c[k - 1] + c[k]) / 2.0;
