@@ -2,6 +2,9 @@
 // work planning, workspace carving and dispatch to the kernels.
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "tcorr_internal.cuh"
 
@@ -19,6 +22,9 @@ int plain_tile_wp();
 
 // Tensor-core path (gram_tc.cu).
 size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method);
+size_t gram_batch_workspace_size(const tcorr_instance *items, int count, int method);
+int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_ws, size_t ws_bytes,
+                   cudaStream_t st);
 int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
              int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st);
 bool gram_method_available(int method);
@@ -104,6 +110,166 @@ int run_corr(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
     return TCORR_OK;
 }
 
+// ------------------------------------------------------------------ batch
+// Plain method: one batched tile launch over every instance's work items
+// (block -> instance by binary search) and one batched reduction.
+struct PlainBatchLayout {
+    std::vector<BandPlan> plans;
+    std::vector<size_t> partial_off;
+    size_t off_args = 0, off_red = 0, total = 0;
+    int64_t total_items = 0, total_lags = 0;
+};
+
+void plain_batch_layout(const tcorr_instance *items, int count, PlainBatchLayout *B) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    B->off_args = take(plain_args_size() * count);
+    B->off_red = take(sizeof(LagReduceDesc) * count);
+    B->plans.resize(count);
+    B->partial_off.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const tcorr_instance &it = items[i];
+        B->plans[i] = make_band_plan(it.T, it.N, it.tau_max, it.stride, plain_tile_bo(), plain_tile_bf(),
+                                     kPlainKseg, kMinItems);
+        B->partial_off[i] = take(sizeof(double) * static_cast<size_t>(B->plans[i].n_items) * B->plans[i].WP);
+        B->total_items += B->plans[i].n_items;
+        B->total_lags += it.tau_max + 1;
+    }
+    B->total = off;
+}
+
+int plain_batch_run(const tcorr_instance *items, int count, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+    PlainBatchLayout B;
+    plain_batch_layout(items, count, &B);
+    if (ws_bytes < B.total || !d_ws) return TCORR_EWORKSPACE;
+    if (B.total_items > 0x7fffffffLL) return TCORR_EUNSUPPORTED;
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    std::vector<uint8_t> args(plain_args_size() * count);
+    std::vector<LagReduceDesc> red(count);
+    int64_t item_begin = 0, lag_begin = 0;
+    for (int i = 0; i < count; ++i) {
+        const tcorr_instance &it = items[i];
+        double *partial = reinterpret_cast<double *>(ws + B.partial_off[i]);
+        plain_args_write(args.data() + plain_args_size() * i, it.kind, it.d_x, B.plans[i], partial, item_begin);
+        red[i] = lag_reduce_desc(B.plans[i], partial, FinalizeArgs{0, nullptr, 0}, it.d_out, lag_begin);
+        item_begin += B.plans[i].n_items;
+        lag_begin += it.tau_max + 1;
+    }
+    cudaError_t e;
+    if ((e = upload_bytes(ws + B.off_args, args.data(), args.size(), st)) != cudaSuccess ||
+        (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * count, st)) != cudaSuccess)
+        return cuda_fail(e, "descriptor upload");
+    if ((e = launch_plain_tiles_batch(ws + B.off_args, count, B.total_items, st)) != cudaSuccess)
+        return cuda_fail(e, "plain_tile_batch_kernel launch");
+    if ((e = launch_lag_reduce_batch(reinterpret_cast<const LagReduceDesc *>(ws + B.off_red), count,
+                                     B.total_lags, st)) != cudaSuccess)
+        return cuda_fail(e, "lag_reduce_batch launch");
+    return TCORR_OK;
+}
+
+int batch_method(const tcorr_instance *items, int count, int method) {
+    if (method != TCORR_AUTO) return method;
+    (void)items;
+    (void)count;
+    return gram_method_available(TCORR_TC_FP16X3) ? TCORR_TC_FP16X3 : TCORR_PLAIN;
+}
+
+size_t batch_workspace(const tcorr_instance *items, int count, int m) {
+    if (m == TCORR_PLAIN) {
+        PlainBatchLayout B;
+        plain_batch_layout(items, count, &B);
+        return B.total;
+    }
+    return gram_batch_workspace_size(items, count, m);
+}
+
+int batch_run_direct(const tcorr_instance *items, int count, int m, void *d_ws, size_t ws_bytes,
+                     cudaStream_t st) {
+    if (m == TCORR_PLAIN) return plain_batch_run(items, count, d_ws, ws_bytes, st);
+    return gram_batch_run(items, count, m, d_ws, ws_bytes, st);
+}
+
+// Graph cache: the first tcorr_batch call with a given argument set is
+// captured into a CUDA graph and instantiated; later calls with the same
+// instances, method, workspace, device and tuning knobs replay it with one
+// cudaGraphLaunch.  Entries are dropped oldest first beyond kGraphCacheSize.
+constexpr size_t kGraphCacheSize = 8;
+
+struct GraphEntry {
+    std::vector<tcorr_instance> items;
+    int method;
+    void *ws;
+    size_t ws_bytes;
+    int device;
+    std::string knobs;
+    cudaGraphExec_t exec;
+};
+
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+
+std::string knob_string() {
+    std::string k;
+    for (const char *name : {"TCORR_KSEG", "TCORR_SUB_KB"}) {
+        const char *v = std::getenv(name);
+        k += v ? v : "-";
+        k += ';';
+    }
+    return k;
+}
+
+bool same_items(const std::vector<tcorr_instance> &a, const tcorr_instance *b, int count) {
+    if (a.size() != static_cast<size_t>(count)) return false;
+    for (int i = 0; i < count; ++i) {
+        const tcorr_instance &x = a[i], &y = b[i];
+        if (x.kind != y.kind || x.d_x != y.d_x || x.T != y.T || x.N != y.N || x.tau_max != y.tau_max ||
+            x.stride != y.stride || x.d_out != y.d_out)
+            return false;
+    }
+    return true;
+}
+
+int batch_run_graph(const tcorr_instance *items, int count, int m, void *d_ws, size_t ws_bytes,
+                    cudaStream_t st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TCORR_ECUDA;
+    const std::string knobs = knob_string();
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (const GraphEntry &g : g_graphs) {
+        if (g.method == m && g.ws == d_ws && g.ws_bytes == ws_bytes && g.device == dev && g.knobs == knobs &&
+            same_items(g.items, items, count)) {
+            const cudaError_t e = cudaGraphLaunch(g.exec, st);
+            return e == cudaSuccess ? TCORR_OK : cuda_fail(e, "cudaGraphLaunch");
+        }
+    }
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const int rc = batch_run_direct(items, count, m, d_ws, ws_bytes, st);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (rc != TCORR_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (g_graphs.size() >= kGraphCacheSize) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(GraphEntry{std::vector<tcorr_instance>(items, items + count), m, d_ws, ws_bytes, dev,
+                                  knobs, exec});
+    e = cudaGraphLaunch(exec, st);
+    return e == cudaSuccess ? TCORR_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
 }  // namespace
 
 // The plain path's plan and size check, shared with the fixed-scratch entry
@@ -166,15 +332,12 @@ int einstein_slope(const double *d_msd, int64_t n, double dt, int dim, int64_t l
 }
 
 size_t tcorr_batch_workspace_size(const tcorr_instance *h_items, int count, int method) {
-    if (!h_items || count < 1) return 0;
-    size_t need = 0;
+    if (!h_items || count < 1 || !known_method(method)) return 0;
     for (int i = 0; i < count; ++i) {
         const tcorr_instance &it = h_items[i];
-        const size_t w = tcorr_workspace_size(it.T, it.N, it.tau_max, it.stride, method);
-        if (w == 0) return 0;
-        if (w > need) need = w;
+        if (!valid_sizes(it.T, it.N, it.tau_max, it.stride)) return 0;
     }
-    return need;
+    return batch_workspace(h_items, count, batch_method(h_items, count, method));
 }
 
 int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws, size_t ws_bytes,
@@ -185,17 +348,20 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
         if ((it.kind != 0 && it.kind != 1) || !it.d_x || !it.d_out ||
             !valid_sizes(it.T, it.N, it.tau_max, it.stride))
             return TCORR_EINVAL;
+        if ((reinterpret_cast<uintptr_t>(it.d_x) & 3u) || (reinterpret_cast<uintptr_t>(it.d_out) & 7u))
+            return TCORR_EALIGN;
     }
-    const size_t need = tcorr_batch_workspace_size(h_items, count, method);
-    if (ws_bytes < need) return TCORR_EWORKSPACE;
-    // Instances run one after another on the stream and share the workspace.
-    for (int i = 0; i < count; ++i) {
-        const tcorr_instance &it = h_items[i];
-        const int rc = run_corr(it.kind, it.d_x, it.T, it.N, it.tau_max, it.stride, method, it.d_out,
-                                d_ws, ws_bytes, stream);
-        if (rc != TCORR_OK) return rc;
-    }
-    return TCORR_OK;
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return TCORR_EALIGN;
+    const int m = batch_method(h_items, count, method);
+    const size_t need = batch_workspace(h_items, count, m);
+    if (need == 0) return TCORR_EUNSUPPORTED;
+    if (ws_bytes < need || !d_ws) return TCORR_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st != nullptr && cudaStreamIsCapturing(st, &cs) != cudaSuccess) return TCORR_ECUDA;
+    if (st == nullptr || cs != cudaStreamCaptureStatusNone || std::getenv("TCORR_NO_GRAPH"))
+        return batch_run_direct(h_items, count, m, d_ws, ws_bytes, st);
+    return batch_run_graph(h_items, count, m, d_ws, ws_bytes, st);
 }
 
 int tcorr_status_poll(void *stream) { return status_poll_and_clear(static_cast<cudaStream_t>(stream)); }

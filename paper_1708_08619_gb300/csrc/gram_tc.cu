@@ -44,6 +44,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "tcorr_internal.cuh"
 
 namespace tcorr {
@@ -278,13 +281,63 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
     return I;
 }
 
+// Where a work item's instance lives: one instance whose tensor maps and
+// arguments are kernel parameters, or a batch of instances described in
+// device memory (item -> instance by binary search over item offsets).
+struct alignas(64) InstDesc {
+    CUtensorMap maps[4];      // A hi, A lo, B hi, B lo
+    GramArgs ga;
+    int64_t item_begin;       // first global work item of this instance
+};
+
+struct SrcSingle {
+    const CUtensorMap *m[4];
+    const GramArgs *a;
+    __device__ __forceinline__ int64_t n_items() const { return a->n_items; }
+    __device__ __forceinline__ const GramArgs *get(int64_t item, int64_t &local, const CUtensorMap *const *&maps) const {
+        local = item;
+        maps = m;
+        return a;
+    }
+};
+
+struct SrcBatch {
+    const InstDesc *d;
+    int n;
+    int64_t total;
+    __device__ __forceinline__ int64_t n_items() const { return total; }
+    __device__ __forceinline__ const GramArgs *get(int64_t item, int64_t &local, const CUtensorMap *&m0) const {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].item_begin <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        local = item - d[lo].item_begin;
+        m0 = d[lo].maps;
+        return &d[lo].ga;
+    }
+};
+
+// Resolve an item to (its instance's arguments, its four tensor maps, local index).
+__device__ __forceinline__ const GramArgs *resolve(const SrcSingle &src, int64_t item, int64_t &local,
+                                                   const CUtensorMap *(&maps)[4]) {
+    local = item;
+    for (int i = 0; i < 4; ++i) maps[i] = src.m[i];
+    return src.a;
+}
+__device__ __forceinline__ const GramArgs *resolve(const SrcBatch &src, int64_t item, int64_t &local,
+                                                   const CUtensorMap *(&maps)[4]) {
+    const CUtensorMap *m0;
+    const GramArgs *a = src.get(item, local, m0);
+    for (int i = 0; i < 4; ++i) maps[i] = m0 + i;
+    return a;
+}
+
 // 10 warps: three share one SM sub-partition's 16K registers, so at most
 // 168 registers per thread (the epilogue keeps 96 FP32 accumulators).
-template <int PREC, bool X4>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    gram_band_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                     GramArgs a) {
+template <int PREC, bool X4, class Src>
+__device__ __forceinline__ void gram_body(const Src &src) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *stages = smem;
@@ -329,30 +382,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int64_t sub_kb = a.sub_kb;
+    const int64_t n_items = src.n_items();
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------- producer
         int st = 0;
         uint32_t ph = 0;
-        for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-            const Item I = decode_item(a, item);
+        for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+            int64_t local;
+            const CUtensorMap *mp[4];
+            const GramArgs &a = *resolve(src, item, local, mp);
+            const Item I = decode_item(a, local);
             if (I.empty) continue;
             for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
                 if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
                 mbar_arrive_expect_tx(full_bar(st), STAGE_BYTES);
                 const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
                 const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
-                tma_load_2d(sbase, &tmAh, kx, static_cast<int32_t>(I.o0), full_bar(st));
-                tma_load_2d(sbase + A_BYTES, &tmAl, kx, static_cast<int32_t>(I.o0), full_bar(st));
+                tma_load_2d(sbase, mp[0], kx, static_cast<int32_t>(I.o0), full_bar(st));
+                tma_load_2d(sbase + A_BYTES, mp[1], kx, static_cast<int32_t>(I.o0), full_bar(st));
                 if (a.b3d) {
-                    tma_load_3d(sbase + 2 * A_BYTES, &tmBh, kx, static_cast<int32_t>(I.rho),
+                    tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx, static_cast<int32_t>(I.rho),
                                 static_cast<int32_t>(I.k0), full_bar(st));
-                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, &tmBl, kx, static_cast<int32_t>(I.rho),
+                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, static_cast<int32_t>(I.rho),
                                 static_cast<int32_t>(I.k0), full_bar(st));
                 } else {
-                    tma_load_2d(sbase + 2 * A_BYTES, &tmBh, kx, static_cast<int32_t>(I.k0), full_bar(st));
-                    tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, &tmBl, kx, static_cast<int32_t>(I.k0),
+                    tma_load_2d(sbase + 2 * A_BYTES, mp[2], kx, static_cast<int32_t>(I.k0), full_bar(st));
+                    tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, static_cast<int32_t>(I.k0),
                                 full_bar(st));
                 }
                 if (++st == STAGES) {
@@ -368,9 +424,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int st = 0;
         uint32_t ph = 0, chain = 0;
         bool issued = false, aborted = false;
-        for (int64_t item = blockIdx.x; item < a.n_items && !aborted; item += gridDim.x) {
-            const Item I = decode_item(a, item);
+        for (int64_t item = blockIdx.x; item < n_items && !aborted; item += gridDim.x) {
+            int64_t local;
+            const CUtensorMap *mp[4];
+            const GramArgs &a = *resolve(src, item, local, mp);
+            const Item I = decode_item(a, local);
             if (I.empty) continue;
+            const int64_t sub_kb = a.sub_kb;
             for (int64_t kc = I.kb0; kc < I.kb1 && !aborted; kc += sub_kb) {
                 const int64_t kc1 = min(I.kb1, kc + sub_kb);
                 const int b = chain & 1;
@@ -427,9 +487,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float *lb = lagbuf + (warp - 2) * WPG;
         uint32_t chain = 0;
         bool aborted = false;
-        for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-            const Item I = decode_item(a, item);
-            double *outp = a.partial + item * WPG;
+        for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+            int64_t local;
+            const CUtensorMap *mp[4];
+            const GramArgs &a = *resolve(src, item, local, mp);
+            const Item I = decode_item(a, local);
+            const int64_t sub_kb = a.sub_kb;
+            double *outp = a.partial + local * WPG;
             if (I.empty) {
                 for (int w = et; w < WPG; w += 32 * NEPI) outp[w] = 0.0;
                 continue;
@@ -505,6 +569,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                      : "memory");
     }
+}
+
+template <int PREC, bool X4>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_band_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                     const __grid_constant__ GramArgs a) {
+    SrcSingle src;
+    src.m[0] = &tmAh;
+    src.m[1] = &tmAl;
+    src.m[2] = &tmBh;
+    src.m[3] = &tmBl;
+    src.a = &a;
+    gram_body<PREC, X4>(src);
+}
+
+template <int PREC, bool X4>
+__global__ void __launch_bounds__(NTHREADS, 1) gram_band_batch_kernel(const __grid_constant__ SrcBatch src) {
+    gram_body<PREC, X4>(src);
 }
 
 // ------------------------------------------------------------------ prep
@@ -590,12 +673,10 @@ __device__ __forceinline__ void load8(const float *__restrict__ row, const float
 }
 
 template <int PREC, int KIND, bool VEC>
-__global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__restrict__ X, int64_t T,
-                                                             int64_t K, int64_t Kp, void *Xh, void *Xl,
-                                                             float *inv_scale, double *S) {
+__device__ __forceinline__ void split_body(const float *__restrict__ X, int64_t T, int64_t K, int64_t Kp,
+                                           void *Xh, void *Xl, float *inv_scale, double *S, int64_t t) {
     __shared__ float red_f[PREP_THREADS / 32];
     __shared__ double red_d[PREP_THREADS / 32];
-    const int64_t t = blockIdx.x;
     const int tid = threadIdx.x;
     const bool live = t < T;
     const float *row = X + (live ? t : 0) * K;
@@ -653,6 +734,44 @@ __global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__rest
     }
 }
 
+template <int PREC, int KIND, bool VEC>
+__global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__restrict__ X, int64_t T,
+                                                             int64_t K, int64_t Kp, void *Xh, void *Xl,
+                                                             float *inv_scale, double *S) {
+    split_body<PREC, KIND, VEC>(X, T, K, Kp, Xh, Xl, inv_scale, S, blockIdx.x);
+}
+
+// One batch entry of the prep pass.
+struct SplitDesc {
+    const float *X;
+    int64_t T, K, Kp;
+    void *Xh, *Xl;
+    float *inv_scale;
+    double *S;
+    int kind, vec;
+    int64_t frame_begin;      // first global block (padded frame) of this instance
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(PREP_THREADS) split_batch_kernel(const SplitDesc *__restrict__ d, int n) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].frame_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const SplitDesc &q = d[lo];
+    const int64_t t = b - q.frame_begin;
+    if (q.kind == 0) {
+        if (q.vec) split_body<PREC, 0, true>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
+        else split_body<PREC, 0, false>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
+    } else {
+        if (q.vec) split_body<PREC, 1, true>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
+        else split_body<PREC, 1, false>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
+    }
+}
+
 // prefix[rho][j] = sum_{j' < j} S(rho + j' s), j = 0 .. n_rho.  One block per
 // residue; each thread owns a contiguous chunk; chunk totals are scanned with
 // a fixed warp-shuffle tree, so the result does not depend on timing.
@@ -682,10 +801,9 @@ __device__ __forceinline__ double block_exclusive_scan(double v, double *warp_to
     return warp_tot[w] + (inc - v);
 }
 
-__global__ void __launch_bounds__(PFX_THREADS) s_prefix_kernel(const double *S, int64_t T, int64_t s,
-                                                                int64_t pstride, double *prefix) {
+__device__ __forceinline__ void s_prefix_body(const double *S, int64_t T, int64_t s, int64_t pstride,
+                                              double *prefix, int64_t rho) {
     __shared__ double warp_tot[32];
-    const int64_t rho = blockIdx.x;
     const int tid = threadIdx.x;
     const int64_t n = n_frames_res(T, s, rho);
     double *pr = prefix + rho * pstride;
@@ -699,6 +817,30 @@ __global__ void __launch_bounds__(PFX_THREADS) s_prefix_kernel(const double *S, 
         run += S[rho + j * s];
         pr[j + 1] = run;
     }
+}
+
+__global__ void __launch_bounds__(PFX_THREADS) s_prefix_kernel(const double *S, int64_t T, int64_t s,
+                                                                int64_t pstride, double *prefix) {
+    s_prefix_body(S, T, s, pstride, prefix, blockIdx.x);
+}
+
+struct PfxDesc {
+    const double *S;
+    int64_t T, s, pstride;
+    double *prefix;
+    int64_t blk_begin;        // first global block (residue) of this instance
+};
+
+__global__ void __launch_bounds__(PFX_THREADS) s_prefix_batch_kernel(const PfxDesc *__restrict__ d, int n) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].blk_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const PfxDesc &q = d[lo];
+    s_prefix_body(q.S, q.T, q.s, q.pstride, q.prefix, b - q.blk_begin);
 }
 
 // ------------------------------------------------------------------ host
@@ -795,82 +937,63 @@ cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, c
     return cudaGetLastError();
 }
 
+template <int PREC, bool X4>
+cudaError_t launch_gram_batch(const SrcBatch &src, int grid, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(gram_band_batch_kernel<PREC, X4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SMEM_TOTAL));
+    if (e != cudaSuccess) return e;
+    gram_band_batch_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(src);
+    return cudaGetLastError();
+}
+
+SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *base, int64_t frame_begin) {
+    SplitDesc q;
+    q.X = X;
+    q.T = L.p.T;
+    q.K = L.p.K;
+    q.Kp = L.Kp;
+    q.Xh = base + L.off_xh;
+    q.Xl = base + L.off_xl;
+    q.inv_scale = reinterpret_cast<float *>(base + L.off_scale);
+    q.S = kind == 0 ? reinterpret_cast<double *>(base + L.off_S) : nullptr;
+    q.kind = kind;
+    q.vec = (q.K % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+    q.frame_begin = frame_begin;
+    return q;
+}
+
 template <int PREC>
-cudaError_t launch_split(int kind, const float *X, const GramLayout &L, uint8_t *ws, cudaStream_t st) {
-    void *xh = ws + L.off_xh, *xl = ws + L.off_xl;
-    float *sc = reinterpret_cast<float *>(ws + L.off_scale);
-    double *S = kind == 0 ? reinterpret_cast<double *>(ws + L.off_S) : nullptr;
-    const int64_t K = L.p.K;
-    const bool vec = (K % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
-    const unsigned g = static_cast<unsigned>(L.T_pad);
-    if (kind == 0) {
-        if (vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
-        else split_kernel<PREC, 0, false><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+cudaError_t launch_split(const SplitDesc &q, int64_t blocks, cudaStream_t st) {
+    const unsigned g = static_cast<unsigned>(blocks);
+    if (q.kind == 0) {
+        if (q.vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
+        else split_kernel<PREC, 0, false><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
     } else {
-        if (vec) split_kernel<PREC, 1, true><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
-        else split_kernel<PREC, 1, false><<<g, PREP_THREADS, 0, st>>>(X, L.p.T, K, L.Kp, xh, xl, sc, S);
+        if (q.vec) split_kernel<PREC, 1, true><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
+        else split_kernel<PREC, 1, false><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
     }
     return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method) {
-    GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, 0, &L)) return 0;
-    return L.total;
-}
-
-bool gram_method_available(int method) {
-    int prec;
-    bool x4;
-    int sms = 0;
-    return method_prec(method, &prec, &x4) && device_is_sm103(&sms) && get_encode() != nullptr;
-}
-
-int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
-    GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, kind, &L)) return TCORR_EUNSUPPORTED;
-    GramLayout Lmax;
-    make_layout(T, N, tau_max, s, method, 0, &Lmax);
-    if (ws_bytes < Lmax.total || !d_ws) return TCORR_EWORKSPACE;
-    int num_sms = 0;
-    if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
+// Tensor maps of one instance: A rows are origins o (frame o s); B rows are
+// frames rho + k s (2-D map for s = 1, (K, residue, frame index) for s > 1).
+int encode_maps(const GramLayout &L, uint8_t *base, int64_t s, CUtensorMap *maps) {
     EncodeFn encode = get_encode();
     if (!encode) return TCORR_EUNSUPPORTED;
-    uint8_t *ws = static_cast<uint8_t *>(d_ws);
-
-    cudaError_t e = cudaSuccess;
-    switch (L.prec) {
-        case P_FP16: e = launch_split<P_FP16>(kind, d_x, L, ws, st); break;
-        case P_BF16: e = launch_split<P_BF16>(kind, d_x, L, ws, st); break;
-        default: e = launch_split<P_TF32>(kind, d_x, L, ws, st); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "split_kernel launch");
-    if (kind == 0) {
-        s_prefix_kernel<<<static_cast<unsigned>(L.p.n_res), PFX_THREADS, 0, st>>>(
-            reinterpret_cast<double *>(ws + L.off_S), T, s, L.pstride, reinterpret_cast<double *>(ws + L.off_prefix));
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "s_prefix_kernel launch");
-    }
-
-    // Tensor maps: A rows are origins o (frame o s); B rows are frames rho + k s.
     const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    CUtensorMap maps[4];
-    void *bases[2] = {ws + L.off_xh, ws + L.off_xl};
+    void *bases[2] = {base + L.off_xh, base + L.off_xl};
     const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kp * L.esize);
+    const cuuint32_t es2[2] = {1, 1};
     for (int h = 0; h < 2; ++h) {
         const cuuint64_t dimA[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.p.n_orig)};
         const cuuint64_t strA[1] = {rowb * static_cast<cuuint64_t>(s)};
         const cuuint32_t boxA[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BO)};
-        const cuuint32_t es2[2] = {1, 1};
-            if (encode(&maps[h], dt, 2, bases[h], dimA, strA, boxA, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        if (encode(&maps[h], dt, 2, bases[h], dimA, strA, boxA, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (A)");
         CUresult rb;
         if (s > 1) {
             const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(s),
@@ -889,9 +1012,12 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
                         CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         }
-        if (rb != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+        if (rb != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (B)");
     }
+    return TCORR_OK;
+}
 
+GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     GramArgs ga;
     ga.T = T;
     ga.s = s;
@@ -903,10 +1029,119 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
     ga.n_items = L.p.n_items;
     ga.kb_total = ceil_div(3 * N, L.bke);
     ga.kb_per_item = L.kseg / L.bke;
-    ga.inv_scale = reinterpret_cast<const float *>(ws + L.off_scale);
-    ga.partial = reinterpret_cast<double *>(ws + L.off_partial);
+    ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
+    ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = s > 1 ? 1 : 0;
     ga.sub_kb = gram_sub_kb();
+    return ga;
+}
+
+FinalizeArgs finalize_args(int kind, const GramLayout &L, uint8_t *base) {
+    FinalizeArgs fa{kind == 0 ? 1 : 0, kind == 0 ? reinterpret_cast<const double *>(base + L.off_prefix) : nullptr,
+                    L.pstride};
+    return fa;
+}
+
+// Batch plan: instances in decreasing order of tensor work (longest first),
+// each with its own workspace region after the descriptor arrays.
+struct BatchLayout {
+    int n = 0, n_msd = 0, prec = 0;
+    bool x4 = false;
+    std::vector<int> order;
+    std::vector<GramLayout> L;
+    std::vector<size_t> base;
+    size_t off_inst = 0, off_split = 0, off_pfx = 0, off_red = 0, total = 0;
+    int64_t total_items = 0, total_frames = 0, total_pfx = 0, total_lags = 0;
+};
+
+bool make_batch_layout(const tcorr_instance *items, int count, int method, BatchLayout *B) {
+    if (!method_prec(method, &B->prec, &B->x4)) return false;
+    B->n = count;
+    B->L.resize(count);
+    std::vector<double> work(count);
+    for (int i = 0; i < count; ++i) {
+        const tcorr_instance &it = items[i];
+        if (!make_layout(it.T, it.N, it.tau_max, it.stride, method, it.kind, &B->L[i])) return false;
+        const BandPlan &p = B->L[i].p;
+        work[i] = static_cast<double>(p.n_res * p.n_rows * p.n_cols) * static_cast<double>(B->L[i].Kp);
+        if (it.kind == 0) ++B->n_msd;
+    }
+    B->order.resize(count);
+    for (int i = 0; i < count; ++i) B->order[i] = i;
+    std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    B->off_inst = take(sizeof(InstDesc) * count);
+    B->off_split = take(sizeof(SplitDesc) * count);
+    B->off_pfx = take(sizeof(PfxDesc) * (B->n_msd > 0 ? B->n_msd : 1));
+    B->off_red = take(sizeof(LagReduceDesc) * count);
+    B->base.resize(count);
+    for (int k = 0; k < count; ++k) {
+        const int i = B->order[k];
+        B->base[i] = take(B->L[i].total);
+        B->total_items += B->L[i].p.n_items;
+        B->total_frames += B->L[i].T_pad;
+        if (items[i].kind == 0) B->total_pfx += B->L[i].p.n_res;
+        B->total_lags += items[i].tau_max + 1;
+    }
+    B->total = off;
+    return B->total_frames < (int64_t(1) << 31) && B->total_items < (int64_t(1) << 40);
+}
+
+}  // namespace
+
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method) {
+    GramLayout L;
+    if (!make_layout(T, N, tau_max, s, method, 0, &L)) return 0;
+    return L.total;
+}
+
+size_t gram_batch_workspace_size(const tcorr_instance *items, int count, int method) {
+    BatchLayout B;
+    if (!make_batch_layout(items, count, method, &B)) return 0;
+    return B.total;
+}
+
+bool gram_method_available(int method) {
+    int prec;
+    bool x4;
+    int sms = 0;
+    return method_prec(method, &prec, &x4) && device_is_sm103(&sms) && get_encode() != nullptr;
+}
+
+int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+    GramLayout L;
+    if (!make_layout(T, N, tau_max, s, method, kind, &L)) return TCORR_EUNSUPPORTED;
+    GramLayout Lmax;
+    make_layout(T, N, tau_max, s, method, 0, &Lmax);
+    if (ws_bytes < Lmax.total || !d_ws) return TCORR_EWORKSPACE;
+    int num_sms = 0;
+    if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+
+    const SplitDesc q = split_desc(kind, d_x, L, ws, 0);
+    cudaError_t e;
+    switch (L.prec) {
+        case P_FP16: e = launch_split<P_FP16>(q, L.T_pad, st); break;
+        case P_BF16: e = launch_split<P_BF16>(q, L.T_pad, st); break;
+        default: e = launch_split<P_TF32>(q, L.T_pad, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "split_kernel launch");
+    if (kind == 0) {
+        s_prefix_kernel<<<static_cast<unsigned>(L.p.n_res), PFX_THREADS, 0, st>>>(
+            reinterpret_cast<double *>(ws + L.off_S), T, s, L.pstride, reinterpret_cast<double *>(ws + L.off_prefix));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "s_prefix_kernel launch");
+    }
+    CUtensorMap maps[4];
+    const int rc = encode_maps(L, ws, s, maps);
+    if (rc != TCORR_OK) return rc;
+    const GramArgs ga = gram_args(L, ws, T, N, tau_max, s);
     const int grid = static_cast<int>(L.p.n_items < num_sms ? L.p.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
         case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st); break;
@@ -915,11 +1150,90 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
         default: e = launch_gram<P_TF32, false>(maps, ga, grid, st); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
-
-    FinalizeArgs fa{kind == 0 ? 1 : 0, kind == 0 ? reinterpret_cast<const double *>(ws + L.off_prefix) : nullptr,
-                    L.pstride};
-    e = launch_lag_reduce(L.p, ga.partial, fa, d_out, st);
+    e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
+    return TCORR_OK;
+}
+
+// Whole batch in four batched launches (prep, S prefix sums, Gram tiles of
+// every instance in one persistent launch, reductions), plus the descriptor
+// uploads.  Callers check arguments; d_ws holds gram_batch_workspace_size().
+int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_ws, size_t ws_bytes,
+                   cudaStream_t st) {
+    BatchLayout B;
+    if (!make_batch_layout(items, count, method, &B)) return TCORR_EUNSUPPORTED;
+    if (ws_bytes < B.total || !d_ws) return TCORR_EWORKSPACE;
+    int num_sms = 0;
+    if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+
+    std::vector<InstDesc> inst(count);
+    std::vector<SplitDesc> spl(count);
+    std::vector<PfxDesc> pfx;
+    std::vector<LagReduceDesc> red(count);
+    int64_t item_begin = 0, frame_begin = 0, pfx_begin = 0, lag_begin = 0;
+    for (int k = 0; k < count; ++k) {
+        const int i = B.order[k];
+        const tcorr_instance &it = items[i];
+        const GramLayout &L = B.L[i];
+        uint8_t *base = ws + B.base[i];
+        const int rc = encode_maps(L, base, it.stride, inst[k].maps);
+        if (rc != TCORR_OK) return rc;
+        inst[k].ga = gram_args(L, base, it.T, it.N, it.tau_max, it.stride);
+        inst[k].item_begin = item_begin;
+        item_begin += L.p.n_items;
+        spl[k] = split_desc(it.kind, it.d_x, L, base, frame_begin);
+        frame_begin += L.T_pad;
+        if (it.kind == 0) {
+            PfxDesc q;
+            q.S = reinterpret_cast<const double *>(base + L.off_S);
+            q.T = it.T;
+            q.s = it.stride;
+            q.pstride = L.pstride;
+            q.prefix = reinterpret_cast<double *>(base + L.off_prefix);
+            q.blk_begin = pfx_begin;
+            pfx_begin += L.p.n_res;
+            pfx.push_back(q);
+        }
+        red[k] = lag_reduce_desc(L.p, inst[k].ga.partial, finalize_args(it.kind, L, base), it.d_out, lag_begin);
+        lag_begin += it.tau_max + 1;
+    }
+    cudaError_t e;
+    if ((e = upload_bytes(ws + B.off_inst, inst.data(), sizeof(InstDesc) * count, st)) != cudaSuccess ||
+        (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * count, st)) != cudaSuccess ||
+        (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * count, st)) != cudaSuccess ||
+        (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx, pfx.data(), sizeof(PfxDesc) * pfx.size(), st)) != cudaSuccess))
+        return cuda_fail(e, "descriptor upload");
+
+    const SplitDesc *d_spl = reinterpret_cast<const SplitDesc *>(ws + B.off_split);
+    const unsigned gs = static_cast<unsigned>(B.total_frames);
+    switch (B.prec) {
+        case P_FP16: split_batch_kernel<P_FP16><<<gs, PREP_THREADS, 0, st>>>(d_spl, count); break;
+        case P_BF16: split_batch_kernel<P_BF16><<<gs, PREP_THREADS, 0, st>>>(d_spl, count); break;
+        default: split_batch_kernel<P_TF32><<<gs, PREP_THREADS, 0, st>>>(d_spl, count); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split_batch_kernel launch");
+    if (!pfx.empty()) {
+        s_prefix_batch_kernel<<<static_cast<unsigned>(B.total_pfx), PFX_THREADS, 0, st>>>(
+            reinterpret_cast<const PfxDesc *>(ws + B.off_pfx), static_cast<int>(pfx.size()));
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "s_prefix_batch_kernel launch");
+    }
+    SrcBatch src;
+    src.d = reinterpret_cast<const InstDesc *>(ws + B.off_inst);
+    src.n = count;
+    src.total = B.total_items;
+    const int grid = static_cast<int>(B.total_items < num_sms ? B.total_items : num_sms);
+    if (grid > 0) {
+        switch (B.prec * 2 + (B.x4 ? 1 : 0)) {
+            case P_FP16 * 2: e = launch_gram_batch<P_FP16, false>(src, grid, st); break;
+            case P_BF16 * 2: e = launch_gram_batch<P_BF16, false>(src, grid, st); break;
+            case P_BF16 * 2 + 1: e = launch_gram_batch<P_BF16, true>(src, grid, st); break;
+            default: e = launch_gram_batch<P_TF32, false>(src, grid, st); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gram_band_batch_kernel launch");
+    }
+    e = launch_lag_reduce_batch(reinterpret_cast<const LagReduceDesc *>(ws + B.off_red), count, B.total_lags, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lag_reduce_batch launch");
     return TCORR_OK;
 }
 

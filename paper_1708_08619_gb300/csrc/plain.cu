@@ -30,12 +30,19 @@ constexpr int PLD = 129;      // floats per row of the flush tile
 constexpr int WP = 256;       // window width stored per item (>= BO+BF-1)
 constexpr size_t SMEM_BYTES = sizeof(float) * (2 * STAGES * BK * LDS + 64 * PLD);
 
+}  // namespace
+
+// One instance of the plain path (also one entry of a batch).
 struct PlainArgs {
     const float *x;
     int64_t T, K, s, tau_max, n_orig;
     int64_t n_res, n_rows, n_cols, kseg, segs_per_item;
-    double *partial;
+    double *partial;        // [n_items][WP] of this instance
+    int64_t item_begin;     // batch: first global block of this instance
+    int kind;               // batch: 0 = MSD, 1 = ACF
 };
+
+namespace {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -57,7 +64,7 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ int swz(int row, int kk) { return row ^ ((kk >> 3) << 4); }
 
 template <int KIND>
-__global__ void __launch_bounds__(NT, 2) plain_tile_kernel(PlainArgs a) {
+__device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item_in) {
     extern __shared__ __align__(16) float smem[];
     float *sA = smem;                              // [STAGES][BK][LDS] origin rows
     float *sB = smem + STAGES * BK * LDS;          // [STAGES][BK][LDS] frame rows
@@ -66,7 +73,7 @@ __global__ void __launch_bounds__(NT, 2) plain_tile_kernel(PlainArgs a) {
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
 
-    int64_t item = blockIdx.x;
+    int64_t item = item_in;
     const int64_t c = item % a.n_cols;
     item /= a.n_cols;
     const int64_t r = item % a.n_rows;
@@ -74,7 +81,7 @@ __global__ void __launch_bounds__(NT, 2) plain_tile_kernel(PlainArgs a) {
     const int64_t rho = item % a.n_res;
     const int64_t g = item / a.n_res;
 
-    double *outp = a.partial + static_cast<int64_t>(blockIdx.x) * WP;
+    double *outp = a.partial + item_in * WP;
     const int64_t n_rho = n_frames_res(a.T, a.s, rho);
     const int64_t m_max = (a.tau_max - rho) / a.s;
     const int64_t o0 = r * BO;
@@ -196,24 +203,36 @@ __global__ void __launch_bounds__(NT, 2) plain_tile_kernel(PlainArgs a) {
     outp[tid] = dacc;
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(NT, 2) plain_tile_kernel(const __grid_constant__ PlainArgs a) {
+    plain_tile_body<KIND>(a, blockIdx.x);
+}
+
+// Batch: block b belongs to the instance whose [item_begin, next item_begin)
+// holds b (binary search over the descriptors); the kind is per instance.
+__global__ void __launch_bounds__(NT, 2) plain_tile_batch_kernel(const PlainArgs *__restrict__ d, int n) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].item_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    __shared__ PlainArgs sa;    // the instance's descriptor, read on demand from shared memory
+    if (threadIdx.x == 0) sa = d[lo];
+    __syncthreads();
+    if (sa.kind == 0) plain_tile_body<0>(sa, b - sa.item_begin);
+    else plain_tile_body<1>(sa, b - sa.item_begin);
+}
+
 }  // namespace
+
+PlainArgs plain_args(int kind, const float *d_x, const BandPlan &p, double *partial, int64_t item_begin);
 
 cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, double *partial,
                                cudaStream_t st) {
     if (p.BO != BO || p.BF != BF || p.WP != WP) return cudaErrorInvalidValue;
-    PlainArgs a;
-    a.x = d_x;
-    a.T = p.T;
-    a.K = p.K;
-    a.s = p.s;
-    a.tau_max = p.tau_max;
-    a.n_orig = p.n_orig;
-    a.n_res = p.n_res;
-    a.n_rows = p.n_rows;
-    a.n_cols = p.n_cols;
-    a.kseg = p.kseg;
-    a.segs_per_item = p.segs_per_item;
-    a.partial = partial;
+    const PlainArgs a = plain_args(kind, d_x, p, partial, 0);
     if (p.n_items <= 0) return cudaSuccess;
     if (p.n_items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
@@ -228,6 +247,43 @@ cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, do
         if (e != cudaSuccess) return e;
         plain_tile_kernel<1><<<static_cast<unsigned>(p.n_items), NT, SMEM_BYTES, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+PlainArgs plain_args(int kind, const float *d_x, const BandPlan &p, double *partial, int64_t item_begin) {
+    PlainArgs a;
+    a.x = d_x;
+    a.T = p.T;
+    a.K = p.K;
+    a.s = p.s;
+    a.tau_max = p.tau_max;
+    a.n_orig = p.n_orig;
+    a.n_res = p.n_res;
+    a.n_rows = p.n_rows;
+    a.n_cols = p.n_cols;
+    a.kseg = p.kseg;
+    a.segs_per_item = p.segs_per_item;
+    a.partial = partial;
+    a.item_begin = item_begin;
+    a.kind = kind;
+    return a;
+}
+
+size_t plain_args_size() { return sizeof(PlainArgs); }
+
+void plain_args_write(void *h_dst, int kind, const float *d_x, const BandPlan &p, double *partial,
+                      int64_t item_begin) {
+    *static_cast<PlainArgs *>(h_dst) = plain_args(kind, d_x, p, partial, item_begin);
+}
+
+cudaError_t launch_plain_tiles_batch(const void *d_descs, int n, int64_t total_items, cudaStream_t st) {
+    if (total_items <= 0) return cudaSuccess;
+    if (total_items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(plain_tile_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    plain_tile_batch_kernel<<<static_cast<unsigned>(total_items), NT, SMEM_BYTES, st>>>(
+        static_cast<const PlainArgs *>(d_descs), n);
     return cudaGetLastError();
 }
 

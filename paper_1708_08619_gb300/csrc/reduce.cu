@@ -6,21 +6,12 @@
 //   gk_integrate -- running trapezoid integral of Eq. 4 (the quadrature loop
 //                   closing Algorithms 8 and 9, which the paper runs on the host);
 //   einstein     -- least-squares slope of the MSD and D = slope / (2d), Eq. 5.
+#include <cstring>
+
 #include "tcorr_internal.cuh"
 
 namespace tcorr {
 namespace {
-
-struct ReduceArgs {
-    const double *partial;
-    int64_t T, N, s, tau_max;
-    int64_t n_res, n_rows, n_cols, n_groups;
-    int BO, BF, WP;
-    int mode;
-    const double *S_prefix;
-    int64_t prefix_stride;
-    double *out;
-};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -30,10 +21,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // One warp per lag.  Lane l sums terms l, l+32, ... in order; the lanes are
 // then combined by a fixed butterfly, so the result does not depend on timing.
-__global__ void lag_reduce_kernel(ReduceArgs a) {
-    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (tau > a.tau_max) return;
+__device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t tau, int lane) {
     const int64_t rho = tau % a.s, m = tau / a.s;
     const int64_t c_lo = m / a.BF;
     int64_t c_hi = (m + a.BO - 1) / a.BF;
@@ -71,6 +59,34 @@ __global__ void lag_reduce_kernel(ReduceArgs a) {
         }
         a.out[tau] = v;
     }
+}
+
+__global__ void lag_reduce_kernel(const __grid_constant__ LagReduceDesc a) {
+    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (tau > a.tau_max) return;
+    lag_reduce_body(a, tau, threadIdx.x & 31);
+}
+
+__global__ void lag_reduce_batch_kernel(const LagReduceDesc *__restrict__ d, int n, int64_t total) {
+    const int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (g >= total) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].lag_begin <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    lag_reduce_body(d[lo], g - d[lo].lag_begin, threadIdx.x & 31);
+}
+
+constexpr int kChunkBytes = 28672;
+struct ByteChunk {
+    uint32_t n;
+    uint8_t bytes[kChunkBytes];
+};
+
+__global__ void write_bytes_kernel(uint8_t *dst, const __grid_constant__ ByteChunk c) {
+    for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.bytes[i];
 }
 
 // Running trapezoid.  One block: thread t owns a contiguous chunk of the
@@ -158,9 +174,9 @@ __global__ void einstein_kernel(const double *msd, double dt, int dim, int64_t l
 
 }  // namespace
 
-cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
-                              double *d_out, cudaStream_t st) {
-    ReduceArgs a;
+LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
+                              double *d_out, int64_t lag_begin) {
+    LagReduceDesc a;
     a.partial = partial;
     a.T = p.T;
     a.N = p.N;
@@ -177,11 +193,43 @@ cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const Fi
     a.S_prefix = fa.S_prefix;
     a.prefix_stride = fa.prefix_stride;
     a.out = d_out;
+    a.lag_begin = lag_begin;
+    return a;
+}
+
+cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
+                              double *d_out, cudaStream_t st) {
+    const LagReduceDesc a = lag_reduce_desc(p, partial, fa, d_out, 0);
     const int64_t warps = p.tau_max + 1;
     const int threads = 256;
     const int64_t blocks = ceil_div(warps * 32, threads);
     lag_reduce_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_lag_reduce_batch(const LagReduceDesc *d_descs, int n, int64_t total_lags,
+                                    cudaStream_t st) {
+    if (total_lags <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = ceil_div(total_lags * 32, threads);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    lag_reduce_batch_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(d_descs, n, total_lags);
+    return cudaGetLastError();
+}
+
+cudaError_t upload_bytes(void *d_dst, const void *h_src, size_t nbytes, cudaStream_t st) {
+    const uint8_t *src = static_cast<const uint8_t *>(h_src);
+    uint8_t *dst = static_cast<uint8_t *>(d_dst);
+    ByteChunk c;
+    for (size_t off = 0; off < nbytes; off += kChunkBytes) {
+        const size_t n = nbytes - off < size_t(kChunkBytes) ? nbytes - off : size_t(kChunkBytes);
+        c.n = static_cast<uint32_t>(n);
+        std::memcpy(c.bytes, src + off, n);
+        write_bytes_kernel<<<1, 256, 0, st>>>(dst + off, c);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,

@@ -74,17 +74,45 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // ([n_items][WP]).  kind 0 = MSD (differences), 1 = ACF (products).
 cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, double *partial,
                                cudaStream_t st);
+// Batch of plain instances: d_descs holds one PlainArgs (plain.cu) per
+// instance, plain_args_size() bytes each, written by plain_args_write.
+size_t plain_args_size();
+void plain_args_write(void *h_dst, int kind, const float *d_x, const BandPlan &p, double *partial,
+                      int64_t item_begin);
+cudaError_t launch_plain_tiles_batch(const void *d_descs, int n, int64_t total_items, cudaStream_t st);
 
 // Fixed-order FP64 reduction of the per-item partials to per-lag sums D(tau),
 // then the normalisation.  mode 0: out = D / (N n_o) (plain MSD and ACF);
 // mode 1: out = (P + Q - 2 D) / (N n_o) using prefix sums of S (Gram MSD).
 struct FinalizeArgs {
     int mode;
-    const double *S_prefix;   // mode 1: [n_res_prefix][...] see gram code
+    const double *S_prefix;   // mode 1: [residue][prefix_stride] prefix sums of S
     int64_t prefix_stride;    // mode 1: entries per residue row of S_prefix
 };
 cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
                               double *d_out, cudaStream_t st);
+
+// One instance of the lag reduction (also one entry of a batch).
+struct LagReduceDesc {
+    const double *partial;
+    int64_t T, N, s, tau_max;
+    int64_t n_res, n_rows, n_cols, n_groups;
+    int BO, BF, WP, mode;
+    const double *S_prefix;
+    int64_t prefix_stride;
+    double *out;
+    int64_t lag_begin;        // batch: first global lag of this instance
+};
+LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
+                              double *d_out, int64_t lag_begin);
+// Batch: one warp per (instance, lag); d_descs in device memory.
+cudaError_t launch_lag_reduce_batch(const LagReduceDesc *d_descs, int n, int64_t total_lags,
+                                    cudaStream_t st);
+
+// Copies host bytes to device memory without a host-to-device memcpy: the
+// bytes travel as kernel parameters (at most 28 KB per launch), so the copy
+// needs no pinned buffer, allocates nothing and can be captured in a graph.
+cudaError_t upload_bytes(void *d_dst, const void *h_src, size_t nbytes, cudaStream_t st);
 
 cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
                                 double *d_running, cudaStream_t st);
