@@ -42,6 +42,9 @@ WORKLOADS = {
     "mid": dict(N=8192, T=5000, tau_max=1000, stride=1, sigma=0.005, box=5.0, gamma=0.05, sites=3,
                 dt=1.0, label="mid-size MSD + VACF + GK + Einstein: N=8192 (3-site molecules), "
                               "T=5000, tau_max=1000, stride 1 (profiling case)"),
+    "batch": dict(label="batching: 256 uneven instances, N log-uniform in [64, 16384], T uniform in "
+                        "[500, 20000], tau_max = T/4, even: MSD of a random walk (sigma 0.01), odd: VACF of "
+                        "OU velocities (gamma uniform in [0.01, 0.5])", count=256, stride=1),
     "small": dict(N=512, T=1000, tau_max=500, stride=1, sigma=0.01, box=3.0, gamma=0.1, sites=1,
                   dt=1.0, label="small MSD + VACF: N=512, T=1000, tau_max=500, stride 1"),
 }
@@ -372,6 +375,109 @@ def run_gpu(args, wl):
         dist.destroy_process_group()
 
 
+def run_batch_workload(args, wl):
+    """One tcorr_batch call (CUDA-graph replay of the batched launches) per step,
+    compared with the same instances run by per-instance tcorr_msd / tcorr_acf calls."""
+    import torch
+    from paper_1708_08619_gb300 import build as tbuild
+    from paper_1708_08619_gb300 import synth, tcorr
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tbuild.build()
+    tcorr.load()
+    rng = np.random.default_rng(synth.BASE_SEED + 4 + rank)
+    items = []
+    u_total = 0
+    for i in range(wl["count"]):
+        N = int(round(np.exp(rng.uniform(np.log(64), np.log(16384)))))
+        Tn = int(rng.integers(500, 20001))
+        tm = Tn // 4
+        seed = synth.BASE_SEED + 1000 * rank + i
+        if i % 2 == 0:
+            x = synth.random_walk_positions_device(Tn, N, 0.01, 3.0, seed, device=dev)
+        else:
+            x = synth.ou_velocities_device(Tn, N, float(rng.uniform(0.01, 0.5)), 1.0, seed, device=dev)
+        out = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+        items.append((i % 2, x, tm, 1, out))
+        u_total += updates(N, Tn, tm, 1)
+    method = args.method
+    inst = tcorr.make_instances(items)
+    need = tcorr.tcorr_batch_workspace_size(inst, method)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            tcorr.tcorr_batch(inst, method, ws=ws, stream=stream)
+        stream.synchronize()
+        sampler = ClockSampler(gpu_identifier(torch, local))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        sampler.start()
+        time.sleep(0.3)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tcorr.tcorr_batch(inst, method, ws=ws, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        clocks = sampler.stop()
+        batch_ms = e0.elapsed_time(e1) / args.steps
+        # the same work as per-instance calls (one workspace sized for the largest instance)
+        del ws
+        need1 = max(tcorr.tcorr_workspace_size(x.shape[0], x.shape[1], tm, s, method)
+                    for _, x, tm, s, _ in items)
+        ws1 = torch.empty(need1, dtype=torch.uint8, device=dev)
+
+        def per_instance():
+            for kind, x, tm, s, out in items:
+                f = tcorr.tcorr_msd if kind == 0 else tcorr.tcorr_acf
+                f(x, tm, s, method, out=out, ws=ws1, stream=stream)
+        per_instance()
+        stream.synchronize()
+        e0.record(stream)
+        reps = max(1, min(3, args.steps))
+        for _ in range(reps):
+            per_instance()
+        e1.record(stream)
+        stream.synchronize()
+        single_ms = e0.elapsed_time(e1) / reps
+    t = torch.tensor([batch_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = u_total * world / (ms / 1000.0)
+    pk, pk_kind = peaks()
+    achieved = 6.0 * u_total / (ms / 1000.0) / 1e12
+    line = {"metric": "atom.origin.lag updates/s (MSD+ACF)", "value": value, "unit": "updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": method, "data": "synthetic",
+            "config": {"workload": wl["label"], "instances": wl["count"], "method": method,
+                       "updates_per_step": u_total, "input_gb": sum(x.numel() * 4 for _, x, *_ in items) / 1e9,
+                       "per_instance_launches_ms": single_ms, "graph_batch_ms": batch_ms,
+                       "batch_speedup_vs_per_instance": single_ms / batch_ms,
+                       "l2": "inputs larger than L2, no flush"},
+            "clocks": clocks, "e2e": None,
+            "gpu_launches": None,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk.get("bf16_tflops", 1900.0),
+                         "unit": "TFLOP/s", "frac": achieved / pk.get("bf16_tflops", 1900.0), "traffic": None,
+                         "kernel": "gram_band_batch_kernel", "note": f"useful Gram FLOPs / batch call time, "
+                                                                    f"{pk_kind} bf16 peak"},
+            "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,6 +492,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.workload == "batch":
+        run_batch_workload(args, wl)
     else:
         run_gpu(args, wl)
 

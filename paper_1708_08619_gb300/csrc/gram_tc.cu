@@ -66,29 +66,30 @@ constexpr int WPG = 320;            // window width per item (>= BO + BF - 1 = 3
 constexpr int NTHREADS = 320;   // 10 warps
 constexpr int NEPI = 8;          // epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int64_t kGramKseg = 4096; // K elements per work item (default)
 constexpr int kSubKb = 3;           // K-blocks per TMEM accumulation sub-chain (default)
 
-// Tuning knobs: TCORR_KSEG (K elements per work item, a multiple of 64) and
-// TCORR_SUB_KB (K-blocks per accumulation sub-chain, 1..8).  Longer
+// Manual overrides: TCORR_KSEG (K elements per work item, a multiple of 64)
+// and TCORR_SUB_KB (K-blocks per accumulation sub-chain, 1..8).  Longer
 // sub-chains trade accuracy for fewer accumulator hand-offs.
-int64_t gram_kseg() {
+int64_t env_kseg() {
     const char *e = std::getenv("TCORR_KSEG");
     const long long v = e ? std::atoll(e) : 0;
-    return (v >= 64 && v % 64 == 0 && v <= (1 << 20)) ? v : kGramKseg;
+    return (v >= 64 && v % 64 == 0 && v <= (1 << 20)) ? v : 0;
 }
-int gram_sub_kb() {
+int env_sub_kb() {
     const char *e = std::getenv("TCORR_SUB_KB");
     const int v = e ? std::atoi(e) : 0;
-    return (v >= 1 && v <= 8) ? v : kSubKb;
+    return (v >= 1 && v <= 8) ? v : 0;
 }
+
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 constexpr size_t SMEM_STAGES = size_t(STAGES) * STAGE_BYTES;
 constexpr size_t SMEM_LAG = NEPI * WPG * sizeof(float);
 constexpr size_t SMEM_CS = BF * sizeof(float);
-constexpr size_t SMEM_BAR = 16 * 8;
-constexpr size_t SMEM_TOTAL = 1024 + SMEM_STAGES + SMEM_LAG + SMEM_CS + SMEM_BAR + 16;
+constexpr size_t SMEM_BAR = 32 * 8;
+constexpr int IQ = 4;               // depth of the work-item queue (producer -> MMA, epilogue)
+constexpr size_t SMEM_TOTAL = 1024 + SMEM_STAGES + SMEM_LAG + SMEM_CS + SMEM_BAR + 16 + IQ * 8;
 
 enum Prec { P_FP16 = 0, P_BF16 = 1, P_TF32 = 2 };
 
@@ -100,6 +101,7 @@ struct GramArgs {
     double *partial;        // [n_items][WPG]
     int b3d;                // B map is 3-D (K, residue, frame index) when s > 1
     int sub_kb;             // K-blocks per accumulation sub-chain
+    unsigned long long *counter;   // work-item counter (zeroed before the launch)
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -165,6 +167,9 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
+}
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -294,6 +299,7 @@ struct SrcSingle {
     const CUtensorMap *m[4];
     const GramArgs *a;
     __device__ __forceinline__ int64_t n_items() const { return a->n_items; }
+    __device__ __forceinline__ unsigned long long *counter() const { return a->counter; }
     __device__ __forceinline__ const GramArgs *get(int64_t item, int64_t &local, const CUtensorMap *const *&maps) const {
         local = item;
         maps = m;
@@ -305,7 +311,9 @@ struct SrcBatch {
     const InstDesc *d;
     int n;
     int64_t total;
+    unsigned long long *ctr;
     __device__ __forceinline__ int64_t n_items() const { return total; }
+    __device__ __forceinline__ unsigned long long *counter() const { return ctr; }
     __device__ __forceinline__ const GramArgs *get(int64_t item, int64_t &local, const CUtensorMap *&m0) const {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
@@ -344,8 +352,9 @@ __device__ __forceinline__ void gram_body(const Src &src) {
     float *lagbuf = reinterpret_cast<float *>(smem + SMEM_STAGES);            // [NEPI][WPG]
     float *cs = reinterpret_cast<float *>(smem + SMEM_STAGES + SMEM_LAG);     // [BF]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SMEM_STAGES + SMEM_LAG + SMEM_CS);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 32);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int64_t *item_q = reinterpret_cast<volatile int64_t *>(tmem_slot + 4);   // [IQ]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
@@ -354,6 +363,8 @@ __device__ __forceinline__ void gram_body(const Src &src) {
     auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
     auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
     const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+    auto iq_full_bar = [&](int q) { return bar0 + 8u * (2 * STAGES + 5 + q); };
+    auto iq_empty_bar = [&](int q) { return bar0 + 8u * (2 * STAGES + 5 + IQ + q); };
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) {
@@ -365,6 +376,10 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             mbar_init(tempty_bar(b), NEPI);
         }
         mbar_init(drain_bar, 1);
+        for (int q = 0; q < IQ; ++q) {
+            mbar_init(iq_full_bar(q), 1);
+            mbar_init(iq_empty_bar(q), 1 + NEPI);   // the MMA thread and one lane per epilogue warp
+        }
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -388,12 +403,27 @@ __device__ __forceinline__ void gram_body(const Src &src) {
         // ---------------------------------------------------------- producer
         int st = 0;
         uint32_t ph = 0;
-        for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const CUtensorMap *last_map = nullptr;
+        unsigned long long *ctr = src.counter();
+        for (uint32_t it = 0;; ++it) {
+            // claim the next work item and publish it to the MMA and epilogue warps
+            const int qs = it % IQ;
+            if (!mbar_wait(iq_empty_bar(qs), ((it / IQ) & 1u) ^ 1u, abort_flag)) goto producer_done;
+            const int64_t claimed = static_cast<int64_t>(atomicAdd(ctr, 1ull));
+            const int64_t item = claimed < n_items ? claimed : -1;
+            item_q[qs] = item;
+            mbar_arrive(iq_full_bar(qs));
+            if (item < 0) break;
             int64_t local;
             const CUtensorMap *mp[4];
             const GramArgs &a = *resolve(src, item, local, mp);
             const Item I = decode_item(a, local);
             if (I.empty) continue;
+            if (mp[0] != last_map) {      // new instance: bring its descriptors close to the TMA unit
+                for (int i = 0; i < 4; ++i) prefetch_tensormap(mp[i]);
+                last_map = mp[0];
+            }
+            const int b3d = a.b3d;
             for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
                 if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
                 mbar_arrive_expect_tx(full_bar(st), STAGE_BYTES);
@@ -401,7 +431,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
                 tma_load_2d(sbase, mp[0], kx, static_cast<int32_t>(I.o0), full_bar(st));
                 tma_load_2d(sbase + A_BYTES, mp[1], kx, static_cast<int32_t>(I.o0), full_bar(st));
-                if (a.b3d) {
+                if (b3d) {
                     tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx, static_cast<int32_t>(I.rho),
                                 static_cast<int32_t>(I.k0), full_bar(st));
                     tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, static_cast<int32_t>(I.rho),
@@ -424,7 +454,12 @@ __device__ __forceinline__ void gram_body(const Src &src) {
         int st = 0;
         uint32_t ph = 0, chain = 0;
         bool issued = false, aborted = false;
-        for (int64_t item = blockIdx.x; item < n_items && !aborted; item += gridDim.x) {
+        for (uint32_t it = 0; !aborted; ++it) {
+            const int qs = it % IQ;
+            if (!mbar_wait(iq_full_bar(qs), (it / IQ) & 1u, abort_flag)) break;
+            const int64_t item = item_q[qs];
+            mbar_arrive(iq_empty_bar(qs));
+            if (item < 0) break;
             int64_t local;
             const CUtensorMap *mp[4];
             const GramArgs &a = *resolve(src, item, local, mp);
@@ -487,7 +522,13 @@ __device__ __forceinline__ void gram_body(const Src &src) {
         float *lb = lagbuf + (warp - 2) * WPG;
         uint32_t chain = 0;
         bool aborted = false;
-        for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        for (uint32_t it = 0;; ++it) {
+            const int qs = it % IQ;
+            if (!mbar_wait(iq_full_bar(qs), (it / IQ) & 1u, abort_flag)) break;
+            const int64_t item = item_q[qs];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(iq_empty_bar(qs));
+            if (item < 0) break;
             int64_t local;
             const CUtensorMap *mp[4];
             const GramArgs &a = *resolve(src, item, local, mp);
@@ -849,7 +890,8 @@ struct GramLayout {
     int prec;
     bool x4;
     int64_t Kp, T_pad, n_k, esize, bke, pstride, kseg;
-    size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, total;
+    int sub_kb;
+    size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, off_counter, total;
 };
 
 bool method_prec(int method, int *prec, bool *x4) {
@@ -870,7 +912,19 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
     L->T_pad = L->n_k * s;           // rows rho + k s for every rho < s, k < n_k exist
-    L->kseg = gram_kseg();
+    // kseg / sub_kb: tuning override, then environment, then tuned cache, then defaults
+    {
+        const BandPlan p0 = make_band_plan(T, N, tau_max, s, BO, BF, 64, 1);
+        const int64_t tiles = p0.n_res * p0.n_rows * p0.n_cols;
+        TuneChoice c{tune_default_kseg(K, tiles), kSubKb};
+        TuneChoice cached;
+        if (const TuneChoice *o = get_tune_override()) c = *o;
+        else if (tune_mode() != 0 && tune_lookup(tune_key(method, kind, K, tau_max, T, s), &cached)) c = cached;
+        if (const int64_t ek = env_kseg()) c.kseg = ek;
+        if (const int es = env_sub_kb()) c.sub_kb = es;
+        L->kseg = c.kseg;
+        L->sub_kb = c.sub_kb;
+    }
     L->p = make_band_plan(T, N, tau_max, s, BO, BF, L->kseg, 1);
     L->p.WP = WPG;
     // one K group per segment of kseg elements
@@ -894,6 +948,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->off_S = take(kind == 0 ? size_t(T) * sizeof(double) : 0);
     L->off_prefix = take(kind == 0 ? size_t(L->p.n_res) * L->pstride * sizeof(double) : 0);
     L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
+    L->off_counter = take(sizeof(unsigned long long));
     L->total = off;
     return true;
 }
@@ -1032,7 +1087,8 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
     ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
     ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = s > 1 ? 1 : 0;
-    ga.sub_kb = gram_sub_kb();
+    ga.sub_kb = L.sub_kb;
+    ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
     return ga;
 }
 
@@ -1050,7 +1106,7 @@ struct BatchLayout {
     std::vector<int> order;
     std::vector<GramLayout> L;
     std::vector<size_t> base;
-    size_t off_inst = 0, off_split = 0, off_pfx = 0, off_red = 0, total = 0;
+    size_t off_inst = 0, off_split = 0, off_pfx = 0, off_red = 0, off_counter = 0, total = 0;
     int64_t total_items = 0, total_frames = 0, total_pfx = 0, total_lags = 0;
 };
 
@@ -1079,6 +1135,7 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     B->off_split = take(sizeof(SplitDesc) * count);
     B->off_pfx = take(sizeof(PfxDesc) * (B->n_msd > 0 ? B->n_msd : 1));
     B->off_red = take(sizeof(LagReduceDesc) * count);
+    B->off_counter = take(sizeof(unsigned long long));
     B->base.resize(count);
     for (int k = 0; k < count; ++k) {
         const int i = B->order[k];
@@ -1094,10 +1151,21 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
 
 }  // namespace
 
+// Workspace bound: the MSD layout (a superset of the ACF one) with the chosen
+// parameters, and with the shortest candidate work item when tuning may run.
 size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method) {
     GramLayout L;
     if (!make_layout(T, N, tau_max, s, method, 0, &L)) return 0;
-    return L.total;
+    size_t need = L.total;
+    if (tune_mode() != 0) {
+        const TuneChoice shortest{tune_min_kseg(), kSubKb};
+        const TuneChoice *prev = get_tune_override();
+        set_tune_override(&shortest);
+        GramLayout Ls;
+        if (make_layout(T, N, tau_max, s, method, 0, &Ls) && Ls.total > need) need = Ls.total;
+        set_tune_override(prev);
+    }
+    return need;
 }
 
 size_t gram_batch_workspace_size(const tcorr_instance *items, int count, int method) {
@@ -1113,13 +1181,13 @@ bool gram_method_available(int method) {
     return method_prec(method, &prec, &x4) && device_is_sm103(&sms) && get_encode() != nullptr;
 }
 
-int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+namespace {
+
+int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+                  double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
     GramLayout L;
     if (!make_layout(T, N, tau_max, s, method, kind, &L)) return TCORR_EUNSUPPORTED;
-    GramLayout Lmax;
-    make_layout(T, N, tau_max, s, method, 0, &Lmax);
-    if (ws_bytes < Lmax.total || !d_ws) return TCORR_EWORKSPACE;
+    if (ws_bytes < L.total || !d_ws) return TCORR_EWORKSPACE;
     int num_sms = 0;
     if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
@@ -1142,6 +1210,8 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
     const int rc = encode_maps(L, ws, s, maps);
     if (rc != TCORR_OK) return rc;
     const GramArgs ga = gram_args(L, ws, T, N, tau_max, s);
+    e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "work-item counter reset");
     const int grid = static_cast<int>(L.p.n_items < num_sms ? L.p.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
         case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st); break;
@@ -1155,9 +1225,72 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
     return TCORR_OK;
 }
 
-// Whole batch in four batched launches (prep, S prefix sums, Gram tiles of
-// every instance in one persistent launch, reductions), plus the descriptor
-// uploads.  Callers check arguments; d_ws holds gram_batch_workspace_size().
+// Times every tuning candidate on the stream (synchronising) and keeps the fastest.
+int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
+              int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, TuneChoice *best) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return TCORR_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TCORR_ECUDA;
+    }
+    float best_ms = -1.f;
+    int rc = TCORR_OK;
+    for (const TuneChoice &c : tune_candidates()) {
+        set_tune_override(&c);
+        rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);   // warm-up
+        if (rc == TCORR_OK) {
+            cudaEventRecord(e0, st);
+            rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);
+            cudaEventRecord(e1, st);
+        }
+        set_tune_override(nullptr);
+        if (rc != TCORR_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = TCORR_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == TCORR_OK) tune_store(key, *best);
+    return rc;
+}
+
+}  // namespace
+
+int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+    const int mode = tune_mode();
+    if (mode != 0 && !env_kseg() && !env_sub_kb()) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            const std::string key = tune_key(method, kind, 3 * N, tau_max, T, s);
+            TuneChoice c;
+            if (mode == 2 || !tune_lookup(key, &c)) {
+                const int rc = gram_tune(key, kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, &c);
+                if (rc != TCORR_OK) return rc;
+            }
+            set_tune_override(&c);
+            const int rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);
+            set_tune_override(nullptr);
+            return rc;
+        }
+    }
+    return gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);
+}
+
+// Whole batch: one batched prep launch, one batched S-prefix launch, Gram
+// tiles (one launch per instance with many work items, one shared
+// persistent launch for the rest), one batched reduction, plus the
+// descriptor uploads.  Callers check arguments; d_ws holds
+// gram_batch_workspace_size().
 int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_ws, size_t ws_bytes,
                    cudaStream_t st) {
     BatchLayout B;
@@ -1167,21 +1300,34 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
 
-    std::vector<InstDesc> inst(count);
+    // Instances with many work items get a launch of their own (tensor maps as
+    // kernel parameters, which the TMA unit reaches faster than maps in
+    // global memory); the rest share one persistent launch.
+    const int64_t big_items = 8 * static_cast<int64_t>(num_sms);
+    std::vector<InstDesc> inst;
+    std::vector<int> big;
     std::vector<SplitDesc> spl(count);
     std::vector<PfxDesc> pfx;
     std::vector<LagReduceDesc> red(count);
+    std::vector<InstDesc> big_desc;
     int64_t item_begin = 0, frame_begin = 0, pfx_begin = 0, lag_begin = 0;
     for (int k = 0; k < count; ++k) {
         const int i = B.order[k];
         const tcorr_instance &it = items[i];
         const GramLayout &L = B.L[i];
         uint8_t *base = ws + B.base[i];
-        const int rc = encode_maps(L, base, it.stride, inst[k].maps);
+        InstDesc d;
+        const int rc = encode_maps(L, base, it.stride, d.maps);
         if (rc != TCORR_OK) return rc;
-        inst[k].ga = gram_args(L, base, it.T, it.N, it.tau_max, it.stride);
-        inst[k].item_begin = item_begin;
-        item_begin += L.p.n_items;
+        d.ga = gram_args(L, base, it.T, it.N, it.tau_max, it.stride);
+        if (L.p.n_items >= big_items) {
+            d.item_begin = 0;
+            big_desc.push_back(d);
+        } else {
+            d.item_begin = item_begin;
+            item_begin += L.p.n_items;
+            inst.push_back(d);
+        }
         spl[k] = split_desc(it.kind, it.d_x, L, base, frame_begin);
         frame_begin += L.T_pad;
         if (it.kind == 0) {
@@ -1195,11 +1341,12 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             pfx_begin += L.p.n_res;
             pfx.push_back(q);
         }
-        red[k] = lag_reduce_desc(L.p, inst[k].ga.partial, finalize_args(it.kind, L, base), it.d_out, lag_begin);
+        red[k] = lag_reduce_desc(L.p, d.ga.partial, finalize_args(it.kind, L, base), it.d_out, lag_begin);
         lag_begin += it.tau_max + 1;
     }
     cudaError_t e;
-    if ((e = upload_bytes(ws + B.off_inst, inst.data(), sizeof(InstDesc) * count, st)) != cudaSuccess ||
+    if ((!inst.empty() &&
+         (e = upload_bytes(ws + B.off_inst, inst.data(), sizeof(InstDesc) * inst.size(), st)) != cudaSuccess) ||
         (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * count, st)) != cudaSuccess ||
         (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * count, st)) != cudaSuccess ||
         (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx, pfx.data(), sizeof(PfxDesc) * pfx.size(), st)) != cudaSuccess))
@@ -1218,12 +1365,27 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             reinterpret_cast<const PfxDesc *>(ws + B.off_pfx), static_cast<int>(pfx.size()));
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "s_prefix_batch_kernel launch");
     }
-    SrcBatch src;
-    src.d = reinterpret_cast<const InstDesc *>(ws + B.off_inst);
-    src.n = count;
-    src.total = B.total_items;
-    const int grid = static_cast<int>(B.total_items < num_sms ? B.total_items : num_sms);
-    if (grid > 0) {
+    for (const InstDesc &d : big_desc) {
+        if ((e = cudaMemsetAsync(d.ga.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+            return cuda_fail(e, "work-item counter reset");
+        const int grid = static_cast<int>(d.ga.n_items < num_sms ? d.ga.n_items : num_sms);
+        switch (B.prec * 2 + (B.x4 ? 1 : 0)) {
+            case P_FP16 * 2: e = launch_gram<P_FP16, false>(d.maps, d.ga, grid, st); break;
+            case P_BF16 * 2: e = launch_gram<P_BF16, false>(d.maps, d.ga, grid, st); break;
+            case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(d.maps, d.ga, grid, st); break;
+            default: e = launch_gram<P_TF32, false>(d.maps, d.ga, grid, st); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
+    }
+    if (!inst.empty() && item_begin > 0) {
+        SrcBatch src;
+        src.d = reinterpret_cast<const InstDesc *>(ws + B.off_inst);
+        src.n = static_cast<int>(inst.size());
+        src.total = item_begin;
+        src.ctr = reinterpret_cast<unsigned long long *>(ws + B.off_counter);
+        if ((e = cudaMemsetAsync(src.ctr, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+            return cuda_fail(e, "work-item counter reset");
+        const int grid = static_cast<int>(src.total < num_sms ? src.total : num_sms);
         switch (B.prec * 2 + (B.x4 ? 1 : 0)) {
             case P_FP16 * 2: e = launch_gram_batch<P_FP16, false>(src, grid, st); break;
             case P_BF16 * 2: e = launch_gram_batch<P_BF16, false>(src, grid, st); break;

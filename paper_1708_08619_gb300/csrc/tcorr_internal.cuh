@@ -21,6 +21,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/tcorr.h"
@@ -65,6 +68,22 @@ inline int cuda_fail(cudaError_t e, const char *what) {
     if (std::getenv("TCORR_VERBOSE")) std::fprintf(stderr, "tcorr: %s: %s\n", what, cudaGetErrorString(e));
     return TCORR_ECUDA;
 }
+
+// Autotuner (tune.cu): per shape bucket, the tensor-core work-item length
+// (kseg, K elements) and accumulation sub-chain length (sub_kb, K-blocks).
+struct TuneChoice {
+    int64_t kseg;
+    int sub_kb;
+};
+int tune_mode();   // 0 off, 1 tune once per bucket, 2 re-tune every call
+std::string tune_key(int method, int kind, int64_t K, int64_t tau_max, int64_t T, int64_t s);
+bool tune_lookup(const std::string &key, TuneChoice *c);
+void tune_store(const std::string &key, const TuneChoice &c);
+const std::vector<TuneChoice> &tune_candidates();
+int64_t tune_min_kseg();
+void set_tune_override(const TuneChoice *c);
+const TuneChoice *get_tune_override();
+int64_t tune_default_kseg(int64_t K, int64_t tiles);
 
 // Workspace layout helpers (byte offsets, 256-byte aligned).
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }

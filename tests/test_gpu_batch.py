@@ -110,3 +110,15 @@ def test_uneven_batch_vs_oracle(T):
             else:
                 scale = ref[-1] if kind == 0 else ref[0]
                 assert np.max(np.abs(got - ref)) / abs(scale) <= parity.TC_TOL, (method, kind, xh.shape)
+
+
+def test_batch_with_a_big_instance(T):
+    """A batch where one instance has enough work items for a launch of its own
+    (N=6000, T=8000, tau_max=2000) next to small ones: bit-identical to single calls."""
+    rng = np.random.default_rng(79)
+    items = uneven_instances(rng, 4, Nmax=300, Tmax=800)
+    items.insert(1, (0, synth.random_walk_positions(8000, 6000, 0.005, 5.0, seed=80), 2000, 1))
+    dev, _ = run_batch(T, items, "fp16x3")
+    for kind, x, tm, s, out in dev:
+        f = T.tcorr_msd if kind == 0 else T.tcorr_acf
+        assert np.array_equal(out.cpu().numpy(), f(x, tm, s, "fp16x3").cpu().numpy()), x.shape
