@@ -102,6 +102,8 @@ struct GramArgs {
     int b3d;                // B map is 3-D (K, residue, frame index) when s > 1
     int sub_kb;             // K-blocks per accumulation sub-chain
     unsigned long long *counter;   // work-item counter (zeroed before the launch)
+    int mode;               // 0 = band tiles, 1 = polyphase blocks
+    int64_t nq;             // polyphase: block shifts q = 0 .. nq-1
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -262,27 +264,65 @@ __host__ __device__ constexpr uint32_t make_idesc() {
            | (static_cast<uint32_t>(BO >> 4) << 24);                       // M >> 4
 }
 
+// One work item, decoded.  A rows start at a_y, B rows at (b_x, b_y, b_z)
+// (b_x: extra K offset; b_z: shifted operand copy, polyphase only).  Entry
+// (row i, column j) of the tile holds band offset / lag m = moff + j - i,
+// kept if 0 <= m <= m_max.  The per-row FP16 scale of row i is
+// inv_scale[sa0 + i*sstr] and of column j inv_scale[sb0 + j*sstr].
 struct Item {
-    int64_t rho, r, c, o0, k0, m_max, kb0, kb1;
+    int64_t rho, a_y, b_x, b_y, b_z, moff, m_max, kb0, kb1;
+    int64_t sa0, sb0, sstr, a_rows;   // a_rows: A rows that hold data (scale lookups)
     bool empty;
 };
 
 __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
     Item I;
     int64_t t = item;
-    I.c = t % a.n_cols;
-    t /= a.n_cols;
-    I.r = t % a.n_rows;
-    t /= a.n_rows;
-    I.rho = t % a.n_res;
-    const int64_t g = t / a.n_res;
-    I.o0 = I.r * BO;
-    I.k0 = I.o0 + I.c * BF;
-    I.m_max = (a.tau_max - I.rho) / a.s;
-    const int64_t n_rho = n_frames_res(a.T, a.s, I.rho);
-    I.kb0 = g * a.kb_per_item;
-    I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
-    I.empty = (I.c * BF - BO + 1 > I.m_max) || (I.k0 >= n_rho) || (I.kb0 >= I.kb1);
+    if (a.mode == 0) {
+        const int64_t c = t % a.n_cols;
+        t /= a.n_cols;
+        const int64_t r = t % a.n_rows;
+        t /= a.n_rows;
+        I.rho = t % a.n_res;
+        const int64_t g = t / a.n_res;
+        const int64_t o0 = r * BO, k0 = o0 + c * BF;
+        I.a_y = o0;
+        I.b_x = 0;
+        I.b_y = k0;
+        I.b_z = I.rho;
+        I.moff = c * BF;
+        I.m_max = (a.tau_max - I.rho) / a.s;
+        I.sa0 = o0 * a.s;
+        I.sb0 = I.rho + k0 * a.s;
+        I.sstr = a.s;
+        I.a_rows = a.n_orig - o0;
+        const int64_t n_rho = n_frames_res(a.T, a.s, I.rho);
+        I.kb0 = g * a.kb_per_item;
+        I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
+        I.empty = (c * BF - BO + 1 > I.m_max) || (k0 >= n_rho) || (I.kb0 >= I.kb1);
+    } else {
+        // polyphase block (q, h, c) of M_q = sum_p Y[.][p] Y[.][p+q]^T, rows = phases
+        const int64_t c = t % 2;
+        t /= 2;
+        const int64_t h = t % 3;
+        t /= 3;
+        const int64_t q = t % a.nq;
+        const int64_t g = t / a.nq;
+        I.rho = 0;
+        I.a_y = BO * h;
+        I.b_x = q - (q & 7);
+        I.b_y = BF * c;
+        I.b_z = q & 7;
+        I.moff = q * (3 * BO) + BF * c - BO * h;
+        I.m_max = a.tau_max;
+        I.sa0 = BO * h;
+        I.sb0 = BF * c;
+        I.sstr = 1;
+        I.a_rows = BO;
+        I.kb0 = g * a.kb_per_item;
+        I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
+        I.empty = (I.moff + BF - 1 < 0) || (I.moff - (BO - 1) > a.tau_max) || (I.kb0 >= I.kb1);
+    }
     return I;
 }
 
@@ -424,22 +464,24 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 last_map = mp[0];
             }
             const int b3d = a.b3d;
+            const int32_t ay = static_cast<int32_t>(I.a_y), by = static_cast<int32_t>(I.b_y);
+            const int32_t bz = static_cast<int32_t>(I.b_z), bx = static_cast<int32_t>(I.b_x);
             for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
                 if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
                 mbar_arrive_expect_tx(full_bar(st), STAGE_BYTES);
                 const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
                 const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
-                tma_load_2d(sbase, mp[0], kx, static_cast<int32_t>(I.o0), full_bar(st));
-                tma_load_2d(sbase + A_BYTES, mp[1], kx, static_cast<int32_t>(I.o0), full_bar(st));
-                if (b3d) {
-                    tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx, static_cast<int32_t>(I.rho),
-                                static_cast<int32_t>(I.k0), full_bar(st));
-                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, static_cast<int32_t>(I.rho),
-                                static_cast<int32_t>(I.k0), full_bar(st));
+                tma_load_2d(sbase, mp[0], kx, ay, full_bar(st));
+                tma_load_2d(sbase + A_BYTES, mp[1], kx, ay, full_bar(st));
+                if (b3d == 2) {          // polyphase: (K + aligned shift, phase row, shifted copy)
+                    tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx + bx, by, bz, full_bar(st));
+                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx + bx, by, bz, full_bar(st));
+                } else if (b3d) {        // band, stride > 1: (K, residue, frame index)
+                    tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx, bz, by, full_bar(st));
+                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, bz, by, full_bar(st));
                 } else {
-                    tma_load_2d(sbase + 2 * A_BYTES, mp[2], kx, static_cast<int32_t>(I.k0), full_bar(st));
-                    tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, static_cast<int32_t>(I.k0),
-                                full_bar(st));
+                    tma_load_2d(sbase + 2 * A_BYTES, mp[2], kx, by, full_bar(st));
+                    tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, by, full_bar(st));
                 }
                 if (++st == STAGES) {
                     st = 0;
@@ -532,17 +574,22 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             int64_t local;
             const CUtensorMap *mp[4];
             const GramArgs &a = *resolve(src, item, local, mp);
-            const Item I = decode_item(a, local);
-            const int64_t sub_kb = a.sub_kb;
-            double *outp = a.partial + local * WPG;
-            if (I.empty) {
-                for (int w = et; w < WPG; w += 32 * NEPI) outp[w] = 0.0;
-                continue;
+            int64_t kb0, kb1;
+            {
+                const Item I0 = decode_item(a, local);
+                if (I0.empty) {
+                    double *outp0 = a.partial + local * WPG;
+                    for (int w = et; w < WPG; w += 32 * NEPI) outp0[w] = 0.0;
+                    continue;
+                }
+                kb0 = I0.kb0;
+                kb1 = I0.kb1;
             }
+            const int64_t sub_kb = a.sub_kb;
             float acc2[BF / 2];
 #pragma unroll
             for (int j = 0; j < BF / 2; ++j) acc2[j] = 0.f;
-            for (int64_t kc = I.kb0; kc < I.kb1; kc += sub_kb) {
+            for (int64_t kc = kb0; kc < kb1; kc += sub_kb) {
                 const int b = chain & 1;
                 if (!mbar_wait(tfull_bar(b), (chain >> 1) & 1u, abort_flag)) {
                     aborted = true;
@@ -569,16 +616,19 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 ++chain;
             }
             if (aborted) break;
+            const Item I = decode_item(a, local);     // decoded again: keeps registers free above
+            double *outp = a.partial + local * WPG;
             float rs = 1.f;
             if (PREC == P_FP16) {
+                const int64_t nscale = a.mode == 0 ? a.T : 3 * BO;
                 for (int j = et; j < BF; j += 32 * NEPI) {
-                    const int64_t f = I.rho + (I.k0 + j) * a.s;
-                    cs[j] = f < a.T ? a.inv_scale[f] : 1.f;
+                    const int64_t f = I.sb0 + j * I.sstr;
+                    cs[j] = f < nscale ? a.inv_scale[f] : 1.f;
                 }
-                rs = (I.o0 + row < a.n_orig) ? a.inv_scale[(I.o0 + row) * a.s] : 1.f;
+                rs = (row < I.a_rows) ? a.inv_scale[I.sa0 + row * I.sstr] : 1.f;
                 named_bar_sync(1, 32 * NEPI);
             }
-            const int64_t mrow = I.c * BF - row;      // band offset m = mrow + j
+            const int64_t mrow = I.moff - row;        // band offset / lag m = mrow + j
 #pragma unroll
             for (int jj = 0; jj < BF / 2; ++jj) {
                 const int j = (BF / 2) * half + jj;
@@ -884,6 +934,130 @@ __global__ void __launch_bounds__(PFX_THREADS) s_prefix_batch_kernel(const PfxDe
     s_prefix_body(q.S, q.T, q.s, q.pstride, q.prefix, b - q.blk_begin);
 }
 
+// ------------------------------------------------------------- polyphase
+// Small K (a few series, e.g. the three off-diagonal pressure components):
+// with L = 384 phases, Y[j][(series, p)] = a_series(p L + j) and
+// M_q = sum_p Y[.][p] Y[.][p+q]^T; entry (j, j') of M_q is the sum of
+// a(t) a(t + tau) over origins t = p L + j with tau = q L + j' - j.  The
+// shift q of the contraction index is split into an aligned part (a TMA
+// coordinate) and q mod 8, served by one of 8 copies of Y pre-shifted by
+// 0..7 elements.  Each series occupies Pp >= P + nq slots of the contraction
+// so that shifted reads never reach the next series.
+constexpr int POLY_L = 3 * BO;       // 384 = 3 row tiles = 2 column tiles
+
+struct PolyPrepArgs {
+    const float *X;
+    int64_t T, K, P, Pp, Kprime, Kalloc;
+    void *Yh, *Yl;                   // [8][L][Kalloc]
+    float *inv_scale;                // [L]
+    int kind;
+};
+
+__device__ __forceinline__ float poly_value(const PolyPrepArgs &a, int64_t j, int64_t kk) {
+    if (kk >= a.Kprime) return 0.f;
+    const int64_t ser = kk / a.Pp, p = kk - ser * a.Pp;
+    const int64_t t = p * POLY_L + j;
+    if (p >= a.P || t >= a.T) return 0.f;
+    const float v = a.X[t * a.K + ser];
+    return a.kind == 0 ? v - a.X[ser] : v;
+}
+
+// One block per (copy r, phase row j): row max (FP16 scale), then hi/lo.
+template <int PREC>
+__global__ void __launch_bounds__(PREP_THREADS) poly_split_kernel(const __grid_constant__ PolyPrepArgs a) {
+    __shared__ float red_f[PREP_THREADS / 32];
+    const int64_t j = blockIdx.x % POLY_L;
+    const int64_t r = blockIdx.x / POLY_L;
+    const int tid = threadIdx.x;
+    float scale = 1.f;
+    if (PREC == P_FP16) {
+        float mx = 0.f;
+        for (int64_t kk = tid; kk < a.Kprime; kk += PREP_THREADS) mx = fmaxf(mx, fabsf(poly_value(a, j, kk)));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if ((tid & 31) == 0) red_f[tid >> 5] = mx;
+        __syncthreads();
+        mx = red_f[0];
+#pragma unroll
+        for (int i = 1; i < PREP_THREADS / 32; ++i) mx = fmaxf(mx, red_f[i]);
+        int e = 0;
+        if (mx > 0.f) {
+            int ex;
+            frexpf(mx, &ex);
+            e = 14 - ex;
+            e = e < -60 ? -60 : (e > 60 ? 60 : e);
+        }
+        scale = ldexpf(1.f, e);
+        if (tid == 0 && r == 0) a.inv_scale[j] = ldexpf(1.f, -e);
+    }
+    const int64_t rowoff = (r * POLY_L + j) * a.Kalloc;
+    for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < a.Kalloc; k0 += PREP_THREADS * 8) {
+        float x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = poly_value(a, j, k0 + i + r);
+        split_store8<PREC>(x, scale, a.Yh, a.Yl, rowoff + k0);
+    }
+}
+
+// S(t) = |x_t|^2 (FP64) for the polyphase MSD: one thread per frame.
+__global__ void poly_s_kernel(const float *X, int64_t T, int64_t K, double *S) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    double acc = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        const double d = static_cast<double>(X[t * K + k] - X[k]);
+        acc += d * d;
+    }
+    S[t] = acc;
+}
+
+struct PolyReduceArgs {
+    const double *partial;
+    int64_t T, N, tau_max, nq, n_groups;
+    int kind;
+    const double *S_prefix;          // kind 0: prefix sums of S, T+1 entries
+    double *out;
+};
+
+// One warp per lag: the blocks (g, q, h, c) whose window holds tau.
+__global__ void poly_reduce_kernel(const __grid_constant__ PolyReduceArgs a) {
+    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (tau > a.tau_max) return;
+    double sum = 0.0;
+    const int64_t nterm = a.n_groups * 6 * 2;     // (g, h, c, q candidate)
+    for (int64_t tt = lane; tt < nterm; tt += 32) {
+        const int64_t cand = tt % 2;
+        const int64_t hc = (tt / 2) % 6;
+        const int64_t g = tt / 12;
+        const int64_t h = hc / 2, c = hc % 2;
+        const int64_t base = tau + BO * h - BF * c + (BO - 1);     // = q L + w
+        const int64_t q = base / POLY_L - cand;
+        if (q < 0 || q >= a.nq) continue;
+        const int64_t w = base - q * POLY_L;
+        if (w < 0 || w > BO + BF - 2) continue;
+        const int64_t item = ((g * a.nq + q) * 3 + h) * 2 + c;
+        sum += a.partial[item * WPG + w];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) {
+        const int64_t no = a.T - tau;
+        const double denom = static_cast<double>(a.N) * static_cast<double>(no);
+        double v;
+        if (a.kind == 1) {
+            v = sum / denom;
+        } else if (tau == 0) {
+            v = 0.0;
+        } else {
+            const double P = a.S_prefix[no];
+            const double Q = a.S_prefix[a.T] - a.S_prefix[tau];
+            v = (P + Q - 2.0 * sum) / denom;
+        }
+        a.out[tau] = v;
+    }
+}
+
 // ------------------------------------------------------------------ host
 struct GramLayout {
     BandPlan p;
@@ -891,6 +1065,8 @@ struct GramLayout {
     bool x4;
     int64_t Kp, T_pad, n_k, esize, bke, pstride, kseg;
     int sub_kb;
+    bool poly;                      // polyphase layout (small K, stride 1)
+    int64_t P, Pp, nq, Kprime, Kalloc;
     size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, off_counter, total;
 };
 
@@ -904,11 +1080,74 @@ bool method_prec(int method, int *prec, bool *x4) {
     }
 }
 
+// Polyphase pays off when K is too small to fill an MMA's K dimension and
+// the lag range spans at least one phase block.
+bool use_polyphase(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
+    if (std::getenv("TCORR_NO_POLYPHASE")) return false;
+    return s == 1 && 3 * N <= 24 && tau_max + 1 >= POLY_L && T >= POLY_L;
+}
+
+bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kind, GramLayout *L) {
+    (void)method;
+    const int64_t K = 3 * N;
+    L->P = ceil_div(T, POLY_L);
+    L->nq = (tau_max + POLY_L - 1) / POLY_L + 1;
+    L->Pp = ceil_div(L->P + L->nq + 1, 64) * 64;
+    L->Kprime = K * L->Pp;
+    L->Kalloc = ceil_div(L->Kprime + L->nq + 8, 64) * 64;
+    L->Kp = L->Kalloc;
+    if (L->Kalloc >= (int64_t(1) << 31)) return false;
+    const int64_t kb_total = ceil_div(L->Kprime, L->bke);
+    {
+        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq), kSubKb};
+        if (const TuneChoice *o = get_tune_override()) c = *o;
+        if (const int64_t ek = env_kseg()) c.kseg = ek;
+        if (const int es = env_sub_kb()) c.sub_kb = es;
+        L->kseg = c.kseg;
+        L->sub_kb = c.sub_kb;
+    }
+    const int64_t kb_per_item = L->kseg / L->bke;
+    L->p = BandPlan{};
+    L->p.T = T;
+    L->p.N = N;
+    L->p.K = K;
+    L->p.tau_max = tau_max;
+    L->p.s = 1;
+    L->p.n_orig = T;
+    L->p.n_res = 1;
+    L->p.BO = BO;
+    L->p.BF = BF;
+    L->p.WP = WPG;
+    L->p.n_groups = ceil_div(kb_total, kb_per_item);
+    L->p.n_items = L->p.n_groups * L->nq * 6;
+    L->T_pad = T;
+    L->n_k = T;
+    L->pstride = T + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t copies = size_t(8) * POLY_L * L->Kalloc * L->esize;
+    L->off_xh = take(copies);
+    L->off_xl = take(copies);
+    L->off_scale = take(size_t(POLY_L) * sizeof(float));
+    L->off_S = take(kind == 0 ? size_t(T) * sizeof(double) : 0);
+    L->off_prefix = take(kind == 0 ? size_t(T + 1) * sizeof(double) : 0);
+    L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
+    L->off_counter = take(sizeof(unsigned long long));
+    L->total = off;
+    return true;
+}
+
 bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int kind, GramLayout *L) {
     if (!method_prec(method, &L->prec, &L->x4)) return false;
     L->esize = L->prec == P_TF32 ? 4 : 2;
     L->bke = L->prec == P_TF32 ? 16 : 32;
     const int64_t K = 3 * N;
+    L->poly = use_polyphase(T, N, tau_max, s);
+    if (L->poly) return make_poly_layout(T, N, tau_max, method, kind, L);
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
     L->T_pad = L->n_k * s;           // rows rho + k s for every rho < s, k < n_k exist
@@ -1073,7 +1312,9 @@ int encode_maps(const GramLayout &L, uint8_t *base, int64_t s, CUtensorMap *maps
 }
 
 GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int64_t tau_max, int64_t s) {
-    GramArgs ga;
+    GramArgs ga{};
+    ga.mode = 0;
+    ga.nq = 0;
     ga.T = T;
     ga.s = s;
     ga.tau_max = tau_max;
@@ -1140,6 +1381,7 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     for (int k = 0; k < count; ++k) {
         const int i = B->order[k];
         B->base[i] = take(B->L[i].total);
+        if (B->L[i].poly) continue;      // polyphase instances run on their own
         B->total_items += B->L[i].p.n_items;
         B->total_frames += B->L[i].T_pad;
         if (items[i].kind == 0) B->total_pfx += B->L[i].p.n_res;
@@ -1147,6 +1389,107 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     }
     B->total = off;
     return B->total_frames < (int64_t(1) << 31) && B->total_items < (int64_t(1) << 40);
+}
+
+// Enqueues one polyphase instance: operand copies, S(t) and its prefix sums
+// (MSD), the Gram kernel over (q, h, c) blocks, and the lag reduction.
+int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, int num_sms,
+             cudaStream_t st) {
+    const int64_t T = L.p.T, N = L.p.N;
+    PolyPrepArgs pa;
+    pa.X = d_x;
+    pa.T = T;
+    pa.K = 3 * N;
+    pa.P = L.P;
+    pa.Pp = L.Pp;
+    pa.Kprime = L.Kprime;
+    pa.Kalloc = L.Kalloc;
+    pa.Yh = base + L.off_xh;
+    pa.Yl = base + L.off_xl;
+    pa.inv_scale = reinterpret_cast<float *>(base + L.off_scale);
+    pa.kind = kind;
+    const unsigned g = 8 * POLY_L;
+    switch (L.prec) {
+        case P_FP16: poly_split_kernel<P_FP16><<<g, PREP_THREADS, 0, st>>>(pa); break;
+        case P_BF16: poly_split_kernel<P_BF16><<<g, PREP_THREADS, 0, st>>>(pa); break;
+        default: poly_split_kernel<P_TF32><<<g, PREP_THREADS, 0, st>>>(pa); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "poly_split_kernel launch");
+    double *S = reinterpret_cast<double *>(base + L.off_S);
+    double *prefix = reinterpret_cast<double *>(base + L.off_prefix);
+    if (kind == 0) {
+        poly_s_kernel<<<static_cast<unsigned>(ceil_div(T, 256)), 256, 0, st>>>(d_x, T, 3 * N, S);
+        s_prefix_kernel<<<1, PFX_THREADS, 0, st>>>(S, T, 1, T + 1, prefix);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly S launch");
+    }
+    EncodeFn encode = get_encode();
+    if (!encode) return TCORR_EUNSUPPORTED;
+    const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUtensorMap maps[4];
+    void *bases[2] = {base + L.off_xh, base + L.off_xl};
+    const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kalloc * L.esize);
+    for (int h = 0; h < 2; ++h) {
+        const cuuint64_t dimA[2] = {static_cast<cuuint64_t>(L.Kalloc), POLY_L};
+        const cuuint64_t strA[1] = {rowb};
+        const cuuint32_t boxA[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BO)};
+        const cuuint32_t es2[2] = {1, 1};
+        if (encode(&maps[h], dt, 2, bases[h], dimA, strA, boxA, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase A)");
+        const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kalloc), POLY_L, 8};
+        const cuuint64_t strB[2] = {rowb, rowb * POLY_L};
+        const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BF), 1};
+        const cuuint32_t es3[3] = {1, 1, 1};
+        if (encode(&maps[2 + h], dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase B)");
+    }
+    GramArgs ga{};
+    ga.T = T;
+    ga.s = 1;
+    ga.tau_max = L.p.tau_max;
+    ga.n_orig = T;
+    ga.n_res = 1;
+    ga.n_rows = 3;
+    ga.n_cols = 2;
+    ga.n_items = L.p.n_items;
+    ga.kb_total = ceil_div(L.Kprime, L.bke);
+    ga.kb_per_item = L.kseg / L.bke;
+    ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
+    ga.partial = reinterpret_cast<double *>(base + L.off_partial);
+    ga.b3d = 2;
+    ga.sub_kb = L.sub_kb;
+    ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
+    ga.mode = 1;
+    ga.nq = L.nq;
+    if ((e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_fail(e, "work-item counter reset");
+    const int grid = static_cast<int>(ga.n_items < num_sms ? ga.n_items : num_sms);
+    switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st); break;
+        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel (polyphase) launch");
+    PolyReduceArgs ra;
+    ra.partial = ga.partial;
+    ra.T = T;
+    ra.N = N;
+    ra.tau_max = L.p.tau_max;
+    ra.nq = L.nq;
+    ra.n_groups = L.p.n_groups;
+    ra.kind = kind;
+    ra.S_prefix = kind == 0 ? prefix : nullptr;
+    ra.out = d_out;
+    poly_reduce_kernel<<<static_cast<unsigned>(ceil_div((L.p.tau_max + 1) * 32, 256)), 256, 0, st>>>(ra);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_reduce launch");
+    return TCORR_OK;
 }
 
 }  // namespace
@@ -1191,6 +1534,7 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     int num_sms = 0;
     if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    if (L.poly) return poly_run(kind, d_x, L, ws, d_out, num_sms, st);
 
     const SplitDesc q = split_desc(kind, d_x, L, ws, 0);
     cudaError_t e;
@@ -1311,11 +1655,17 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     std::vector<LagReduceDesc> red(count);
     std::vector<InstDesc> big_desc;
     int64_t item_begin = 0, frame_begin = 0, pfx_begin = 0, lag_begin = 0;
+    std::vector<int> poly;
+    int nb = 0;                          // band instances, in descriptor order
     for (int k = 0; k < count; ++k) {
         const int i = B.order[k];
         const tcorr_instance &it = items[i];
         const GramLayout &L = B.L[i];
         uint8_t *base = ws + B.base[i];
+        if (L.poly) {
+            poly.push_back(i);
+            continue;
+        }
         InstDesc d;
         const int rc = encode_maps(L, base, it.stride, d.maps);
         if (rc != TCORR_OK) return rc;
@@ -1328,7 +1678,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             item_begin += L.p.n_items;
             inst.push_back(d);
         }
-        spl[k] = split_desc(it.kind, it.d_x, L, base, frame_begin);
+        spl[nb] = split_desc(it.kind, it.d_x, L, base, frame_begin);
         frame_begin += L.T_pad;
         if (it.kind == 0) {
             PfxDesc q;
@@ -1341,23 +1691,29 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             pfx_begin += L.p.n_res;
             pfx.push_back(q);
         }
-        red[k] = lag_reduce_desc(L.p, d.ga.partial, finalize_args(it.kind, L, base), it.d_out, lag_begin);
+        red[nb] = lag_reduce_desc(L.p, d.ga.partial, finalize_args(it.kind, L, base), it.d_out, lag_begin);
         lag_begin += it.tau_max + 1;
+        ++nb;
     }
+    for (int i : poly) {
+        const int rc = poly_run(items[i].kind, items[i].d_x, B.L[i], ws + B.base[i], items[i].d_out, num_sms, st);
+        if (rc != TCORR_OK) return rc;
+    }
+    if (nb == 0) return TCORR_OK;
     cudaError_t e;
     if ((!inst.empty() &&
          (e = upload_bytes(ws + B.off_inst, inst.data(), sizeof(InstDesc) * inst.size(), st)) != cudaSuccess) ||
-        (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * count, st)) != cudaSuccess ||
-        (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * count, st)) != cudaSuccess ||
+        (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * nb, st)) != cudaSuccess ||
+        (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * nb, st)) != cudaSuccess ||
         (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx, pfx.data(), sizeof(PfxDesc) * pfx.size(), st)) != cudaSuccess))
         return cuda_fail(e, "descriptor upload");
 
     const SplitDesc *d_spl = reinterpret_cast<const SplitDesc *>(ws + B.off_split);
     const unsigned gs = static_cast<unsigned>(B.total_frames);
     switch (B.prec) {
-        case P_FP16: split_batch_kernel<P_FP16><<<gs, PREP_THREADS, 0, st>>>(d_spl, count); break;
-        case P_BF16: split_batch_kernel<P_BF16><<<gs, PREP_THREADS, 0, st>>>(d_spl, count); break;
-        default: split_batch_kernel<P_TF32><<<gs, PREP_THREADS, 0, st>>>(d_spl, count); break;
+        case P_FP16: split_batch_kernel<P_FP16><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
+        case P_BF16: split_batch_kernel<P_BF16><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
+        default: split_batch_kernel<P_TF32><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split_batch_kernel launch");
     if (!pfx.empty()) {
@@ -1394,7 +1750,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         }
         if (e != cudaSuccess) return cuda_fail(e, "gram_band_batch_kernel launch");
     }
-    e = launch_lag_reduce_batch(reinterpret_cast<const LagReduceDesc *>(ws + B.off_red), count, B.total_lags, st);
+    e = launch_lag_reduce_batch(reinterpret_cast<const LagReduceDesc *>(ws + B.off_red), nb, B.total_lags, st);
     if (e != cudaSuccess) return cuda_fail(e, "lag_reduce_batch launch");
     return TCORR_OK;
 }
