@@ -45,6 +45,9 @@ WORKLOADS = {
     "batch": dict(label="batching: 256 uneven instances, N log-uniform in [64, 16384], T uniform in "
                         "[500, 20000], tau_max = T/4, even: MSD of a random walk (sigma 0.01), odd: VACF of "
                         "OU velocities (gamma uniform in [0.01, 0.5])", count=256, stride=1),
+    "flux": dict(label="Green-Kubo flux ACF: (Pxy, Pxz, Pyz) as [T][1][3], AR(1) phi=0.999 unit variance, "
+                       "T=2,000,000 plus 64 series of T=200,000, tau_max=20,000, ACF + running viscosity "
+                       "integral", T=2000000, Tshort=200000, nshort=64, tau_max=20000, phi=0.999),
     "small": dict(N=512, T=1000, tau_max=500, stride=1, sigma=0.01, box=3.0, gamma=0.1, sites=1,
                   dt=1.0, label="small MSD + VACF: N=512, T=1000, tau_max=500, stride 1"),
 }
@@ -478,6 +481,92 @@ def run_batch_workload(args, wl):
         dist.destroy_process_group()
 
 
+def run_flux_workload(args, wl):
+    """ACF of one long flux series plus a batch of 64 shorter ones, and the running
+    Green-Kubo integral of every result, per step."""
+    import torch
+    from paper_1708_08619_gb300 import build as tbuild
+    from paper_1708_08619_gb300 import synth, tcorr
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tbuild.build()
+    tcorr.load()
+    tm = wl["tau_max"]
+    longh = synth.ar1_flux(wl["T"], wl["phi"], seed=synth.BASE_SEED + 6 + 100 * rank)
+    shorth = [synth.ar1_flux(wl["Tshort"], wl["phi"], seed=synth.BASE_SEED + 1000 + 100 * rank + i)
+              for i in range(wl["nshort"])]
+    xl = torch.from_numpy(longh).to(dev)
+    xs = [torch.from_numpy(a).to(dev) for a in shorth]
+    u = updates(1, wl["T"], tm, 1) + wl["nshort"] * updates(1, wl["Tshort"], tm, 1)
+    stream = torch.cuda.Stream(dev)
+    res = {}
+    for method in (args.method, "plain"):
+        outs = [torch.empty(tm + 1, dtype=torch.float64, device=dev) for _ in range(1 + wl["nshort"])]
+        gks = [torch.empty(tm + 1, dtype=torch.float64, device=dev) for _ in range(1 + wl["nshort"])]
+        items = [(1, x, tm, 1, o) for x, o in zip(xs, outs[1:])]
+        inst = tcorr.make_instances(items)
+        ws_b = torch.empty(max(256, tcorr.tcorr_batch_workspace_size(inst, method)), dtype=torch.uint8, device=dev)
+        ws_l = torch.empty(max(256, tcorr.tcorr_workspace_size(wl["T"], 1, tm, 1, method)), dtype=torch.uint8,
+                           device=dev)
+        with torch.cuda.stream(stream):
+            def step():
+                tcorr.tcorr_acf(xl, tm, 1, method, out=outs[0], ws=ws_l, stream=stream)
+                tcorr.tcorr_batch(inst, method, ws=ws_b, stream=stream)
+                for o, g in zip(outs, gks):
+                    tcorr.gk_integrate(o, 1.0, 1.0 / 3.0, out=g, stream=stream)
+            for _ in range(max(3, args.warmup)):
+                step()
+            stream.synchronize()
+            steps = args.steps if method == args.method else max(1, min(2, args.steps))
+            sampler = ClockSampler(gpu_identifier(torch, local)) if method == args.method else None
+            if sampler:
+                sampler.start()
+                time.sleep(0.3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            stream.synchronize()
+            clocks = sampler.stop() if sampler else None
+        res[method] = (e0.elapsed_time(e1) / steps, clocks, outs[0].cpu().numpy())
+        del ws_b, ws_l
+    ms, clocks, c_tc = res[args.method]
+    p_ms, _, c_plain = res["plain"]
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = u * world / (ms / 1000.0)
+    pk, pk_kind = peaks()
+    achieved = 6.0 * u / (ms / 1000.0) / 1e12
+    line = {"metric": "origin.lag pairs/s of the 3-component flux ACF", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.method,
+            "data": "synthetic",
+            "config": {"workload": wl["label"], "pairs_per_step": u, "plain_ms_per_step": p_ms,
+                       "speedup_vs_plain": p_ms / ms,
+                       "max_diff_tc_vs_plain_over_C0": float(np.max(np.abs(c_tc - c_plain)) / abs(c_plain[0])),
+                       "l2": "long series 24 MB (fits L2); operand copies 0.2 GB"},
+            "clocks": clocks, "e2e": None, "gpu_launches": None,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk.get("bf16_tflops", 1900.0),
+                         "unit": "TFLOP/s", "frac": achieved / pk.get("bf16_tflops", 1900.0), "traffic": None,
+                         "kernel": "gram_band_kernel (polyphase)",
+                         "note": f"useful FLOPs (6 per pair) / step time, {pk_kind} bf16 peak"},
+            "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,6 +583,8 @@ def main():
         run_reference(args, wl)
     elif args.workload == "batch":
         run_batch_workload(args, wl)
+    elif args.workload == "flux":
+        run_flux_workload(args, wl)
     else:
         run_gpu(args, wl)
 
