@@ -1,0 +1,71 @@
+"""Multi-rank host logic on CPU with two gloo ranks: instance sharding and the
+max-over-ranks timing used by the benchmark harness."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1708_08619_gb300 import shard
+
+torch = pytest.importorskip("torch")
+
+
+def test_instance_work_matches_definition():
+    T, N, tm, s = 37, 5, 20, 3
+    want = N * sum(len(range(0, T - tau, s)) for tau in range(tm + 1))
+    assert shard.instance_work(T, N, tm, s) == want
+
+
+def test_partition_is_complete_disjoint_and_balanced():
+    rng = np.random.default_rng(5)
+    works = [int(w) for w in rng.integers(1, 10 ** 6, size=257)]
+    for world in (1, 2, 3, 8):
+        shares = shard.partition(works, world)
+        flat = sorted(i for s in shares for i in s)
+        assert flat == list(range(len(works)))
+        loads = [sum(works[i] for i in s) for s in shares]
+        assert max(loads) - min(loads) <= max(works)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, shapes, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mine = shard.my_share(shapes, rank, world)
+    t = shard.max_over_ranks(10.0 + rank)
+    # gather every rank's share on every rank to check coverage
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    dist.destroy_process_group()
+    q.put((rank, mine, t, gathered))
+
+
+def test_two_gloo_ranks_share_a_batch_and_agree_on_the_step_time():
+    import torch.multiprocessing as mp
+    rng = np.random.default_rng(7)
+    shapes = [(int(rng.integers(100, 2000)), int(rng.integers(1, 500)), 0, 1) for _ in range(40)]
+    shapes = [(T, N, T // 4, 1) for T, N, _, _ in shapes]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, shapes, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    results.sort()
+    for rank, mine, t, gathered in results:
+        assert t == 11.0                      # max over ranks of 10 + rank
+        flat = sorted(i for s in gathered for i in s)
+        assert flat == list(range(len(shapes)))
+        assert gathered[rank] == mine
