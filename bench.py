@@ -39,6 +39,9 @@ WORKLOADS = {
                   sites=3, dt=1.0,
                   label="water-scale MSD + VACF + GK + Einstein: N=32768 (3-site molecules), "
                         "T=10000, tau_max=2000, stride 1"),
+    "water8": dict(N=4096, T=10000, tau_max=2000, stride=1, sigma=0.005, box=5.0, gamma=0.05, sites=3,
+                   dt=1.0, label="water-scale with 1/8 of the atoms (profiling case): N=4096 (3-site "
+                                 "molecules), T=10000, tau_max=2000, stride 1"),
     "mid": dict(N=8192, T=5000, tau_max=1000, stride=1, sigma=0.005, box=5.0, gamma=0.05, sites=3,
                 dt=1.0, label="mid-size MSD + VACF + GK + Einstein: N=8192 (3-site molecules), "
                               "T=5000, tau_max=1000, stride 1 (profiling case)"),
@@ -118,6 +121,12 @@ def gpu_identifier(torch, dev):
         return u if u.startswith("GPU-") else "GPU-" + u
     except Exception:
         return dev
+
+
+# DRAM bytes (read + write) of one water-scale MSD launch of the tensor-core band kernel (FP16 x3),
+# from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
+# see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
+GRAM_WATER_TRAFFIC_BYTES = 8 * (1014.019e6 + 5.692e6)
 
 
 def peaks():
@@ -312,8 +321,10 @@ def run_gpu(args, wl):
         flops = 6.0 * u_res   # useful Gram flops: 3 MACs per update
         peak_t = pk.get("bf16_tflops", 1900.0)
         achieved = flops / msd_avg_s / 1e12
+        traffic = (GRAM_WATER_TRAFFIC_BYTES if (method == "fp16x3" and args.workload == "water")
+                   else None)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
-                "frac": achieved / peak_t, "traffic": None, "kernel": "gram_band_tc<MSD>",
+                "frac": achieved / peak_t, "traffic": traffic, "kernel": "gram_band_tc<MSD>",
                 "note": f"useful Gram FLOPs (6 per update) / MSD call time vs {pk_kind} "
                         f"bf16 dense burst peak; issued tensor FLOPs are 3x (split) plus band waste"}
 
