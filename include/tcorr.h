@@ -193,6 +193,19 @@ int tcorr_plain_static(int kind, const float *d_x, int64_t T, int64_t N, int64_t
  */
 int tcorr_status_poll(void *stream);
 
+/*
+ * Diagnostics, with no counterpart in the paper: when enabled, the library
+ * records a pair of CUDA events on the launching stream around every launch
+ * of its dominant kernel (the tensor-core band / polyphase kernel or the
+ * plain tile kernel; not while the stream is being captured), so that a
+ * caller can time that kernel alone.  tcorr_profile_read waits for the
+ * recorded launches of one kind (0 = MSD, 1 = autocorrelation, 2 = batched
+ * launches mixing both), returns their summed duration in milliseconds and
+ * their count, and forgets them.  Errors: TCORR_EINVAL, TCORR_ECUDA.
+ */
+int tcorr_profile_enable(int on);
+int tcorr_profile_read(int kind, double *total_ms, int *launches);
+
 /* Human-readable name of a tcorr_status value (static string). */
 const char *tcorr_strerror(int code);
 

@@ -1223,11 +1223,13 @@ bool device_is_sm103(int *num_sms) {
 }
 
 template <int PREC, bool X4>
-cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, cudaStream_t st) {
+cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, cudaStream_t st, int kind) {
     cudaError_t e = cudaFuncSetAttribute(gram_band_kernel<PREC, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(SMEM_TOTAL));
     if (e != cudaSuccess) return e;
+    prof_begin(kind, st);
     gram_band_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(maps[0], maps[1], maps[2], maps[3], ga);
+    prof_end(st);
     return cudaGetLastError();
 }
 
@@ -1236,7 +1238,9 @@ cudaError_t launch_gram_batch(const SrcBatch &src, int grid, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(gram_band_batch_kernel<PREC, X4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SMEM_TOTAL));
     if (e != cudaSuccess) return e;
+    prof_begin(2, st);
     gram_band_batch_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(src);
+    prof_end(st);
     return cudaGetLastError();
 }
 
@@ -1471,10 +1475,10 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
         return cuda_fail(e, "work-item counter reset");
     const int grid = static_cast<int>(ga.n_items < num_sms ? ga.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
-        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st); break;
-        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st); break;
-        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st); break;
-        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st); break;
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st, kind); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st, kind); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st, kind); break;
+        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st, kind); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel (polyphase) launch");
     PolyReduceArgs ra;
@@ -1558,10 +1562,10 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     if (e != cudaSuccess) return cuda_fail(e, "work-item counter reset");
     const int grid = static_cast<int>(L.p.n_items < num_sms ? L.p.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
-        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st); break;
-        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st); break;
-        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st); break;
-        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st); break;
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st, kind); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st, kind); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st, kind); break;
+        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st, kind); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
     e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st);
@@ -1726,10 +1730,10 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             return cuda_fail(e, "work-item counter reset");
         const int grid = static_cast<int>(d.ga.n_items < num_sms ? d.ga.n_items : num_sms);
         switch (B.prec * 2 + (B.x4 ? 1 : 0)) {
-            case P_FP16 * 2: e = launch_gram<P_FP16, false>(d.maps, d.ga, grid, st); break;
-            case P_BF16 * 2: e = launch_gram<P_BF16, false>(d.maps, d.ga, grid, st); break;
-            case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(d.maps, d.ga, grid, st); break;
-            default: e = launch_gram<P_TF32, false>(d.maps, d.ga, grid, st); break;
+            case P_FP16 * 2: e = launch_gram<P_FP16, false>(d.maps, d.ga, grid, st, 2); break;
+            case P_BF16 * 2: e = launch_gram<P_BF16, false>(d.maps, d.ga, grid, st, 2); break;
+            case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(d.maps, d.ga, grid, st, 2); break;
+            default: e = launch_gram<P_TF32, false>(d.maps, d.ga, grid, st, 2); break;
         }
         if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
     }

@@ -240,12 +240,16 @@ cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, do
         e = cudaFuncSetAttribute(plain_tile_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(SMEM_BYTES));
         if (e != cudaSuccess) return e;
+        prof_begin(0, st);
         plain_tile_kernel<0><<<static_cast<unsigned>(p.n_items), NT, SMEM_BYTES, st>>>(a);
+        prof_end(st);
     } else {
         e = cudaFuncSetAttribute(plain_tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(SMEM_BYTES));
         if (e != cudaSuccess) return e;
+        prof_begin(1, st);
         plain_tile_kernel<1><<<static_cast<unsigned>(p.n_items), NT, SMEM_BYTES, st>>>(a);
+        prof_end(st);
     }
     return cudaGetLastError();
 }

@@ -85,6 +85,11 @@ void set_tune_override(const TuneChoice *c);
 const TuneChoice *get_tune_override();
 int64_t tune_default_kseg(int64_t K, int64_t tiles);
 
+// Diagnostics (profile.cu): events around one launch of the dominant kernel.
+// kind: 0 MSD, 1 ACF, 2 a batched launch mixing both.
+void prof_begin(int kind, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
 // Workspace layout helpers (byte offsets, 256-byte aligned).
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 

@@ -59,6 +59,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tcorr_batch.restype = ci
     lib.tcorr_plain_static.argtypes = [ci, vp, i64, i64, i64, i64, vp, vp]
     lib.tcorr_plain_static.restype = ci
+    lib.tcorr_profile_enable.argtypes = [ci]
+    lib.tcorr_profile_enable.restype = ci
+    lib.tcorr_profile_read.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.tcorr_profile_read.restype = ci
     lib.tcorr_status_poll.argtypes = [vp]
     lib.tcorr_status_poll.restype = ci
     lib.tcorr_strerror.argtypes = [ci]
@@ -206,6 +210,21 @@ def tcorr_plain_static(kind: int, x, tau_max: int, stride: int = 1, out=None, st
     if rc != 0:
         raise TcorrError(rc, "tcorr_plain_static")
     return out
+
+
+def tcorr_profile_enable(on: bool = True) -> None:
+    """Record CUDA events around every launch of the dominant kernel (diagnostics)."""
+    load().tcorr_profile_enable(1 if on else 0)
+
+
+def tcorr_profile_read(kind: int):
+    """(summed milliseconds, launches) of the recorded dominant-kernel launches of one kind."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int()
+    rc = load().tcorr_profile_read(kind, ctypes.byref(ms), ctypes.byref(n))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_profile_read")
+    return ms.value, n.value
 
 
 def tcorr_status_poll(stream=None) -> int:

@@ -135,3 +135,19 @@ def test_water_scale_sampled_lags(T):
     assert m[0] == 0.0
     assert np.max(np.abs(m[lags[1:]] - rm[1:]) / rm[1:]) <= parity.PLAIN_TOL
     assert np.max(np.abs(c[lags] - rc)) / abs(rc[0]) <= parity.PLAIN_TOL
+
+
+def test_profile_hooks_time_the_dominant_kernel(T):
+    x = dev(synth.random_walk_positions(800, 300, 0.01, 3.0, seed=12))
+    T.tcorr_profile_enable(True)
+    T.tcorr_profile_read(0)
+    T.tcorr_profile_read(1)
+    for _ in range(3):
+        T.tcorr_msd(x, 300, 1, "plain")
+    T.tcorr_acf(x, 300, 1, "plain")
+    ms0, n0 = T.tcorr_profile_read(0)
+    ms1, n1 = T.tcorr_profile_read(1)
+    T.tcorr_profile_enable(False)
+    T.tcorr_msd(x, 300, 1, "plain")
+    assert n0 == 3 and n1 == 1 and ms0 > 0 and ms1 > 0
+    assert T.tcorr_profile_read(0) == (0.0, 0)
