@@ -206,6 +206,15 @@ int tcorr_status_poll(void *stream);
 int tcorr_profile_enable(int on);
 int tcorr_profile_read(int kind, double *total_ms, int *launches);
 
+/*
+ * Self-test of the device-side error path, with no counterpart in the paper:
+ * enqueues one tiny kernel that waits on a barrier nothing completes; after
+ * 10 ms the bounded wait gives up, the kernel records TCORR_ETIMEOUT in the
+ * status word and returns (no trap, the context stays usable).  The next
+ * tcorr_status_poll returns TCORR_ETIMEOUT.  Errors: TCORR_ECUDA.
+ */
+int tcorr_selftest_timeout(void *stream);
+
 /* Human-readable name of a tcorr_status value (static string). */
 const char *tcorr_strerror(int code);
 

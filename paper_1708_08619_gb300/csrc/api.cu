@@ -29,6 +29,7 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
              int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st);
 bool gram_method_available(int method);
 int status_poll_and_clear(cudaStream_t st);
+int selftest_timeout(cudaStream_t st);
 
 BandPlan make_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int BO, int BF,
                         int64_t kseg, int64_t min_items) {
@@ -365,6 +366,8 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
 }
 
 int tcorr_status_poll(void *stream) { return status_poll_and_clear(static_cast<cudaStream_t>(stream)); }
+
+int tcorr_selftest_timeout(void *stream) { return selftest_timeout(static_cast<cudaStream_t>(stream)); }
 
 const char *tcorr_strerror(int code) {
     switch (code) {

@@ -1759,6 +1759,37 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     return TCORR_OK;
 }
 
+namespace {
+
+// Waits on an mbarrier that nothing completes, with a short limit, through the
+// same bounded-wait path as the band kernel: the wait gives up, the status
+// word records TCORR_ETIMEOUT, and the kernel returns normally.
+__global__ void timeout_probe_kernel(unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    fence_barrier_init();
+    abort_flag = 0;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(b, 0u)) return;              // never: nobody arrives
+        if ((it & 255u) == 255u && globaltimer() - t0 > limit_ns) {
+            atomicExch(&g_status, static_cast<unsigned int>(TCORR_ETIMEOUT));
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+int selftest_timeout(cudaStream_t st) {
+    timeout_probe_kernel<<<1, 32, 0, st>>>(10000000ull);   // 10 ms
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TCORR_OK : cuda_fail(e, "timeout_probe_kernel launch");
+}
+
 int status_poll_and_clear(cudaStream_t st) {
     if (cudaStreamSynchronize(st) != cudaSuccess) return TCORR_ECUDA;
     unsigned int v = 0;

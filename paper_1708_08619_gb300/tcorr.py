@@ -63,6 +63,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tcorr_profile_enable.restype = ci
     lib.tcorr_profile_read.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.tcorr_profile_read.restype = ci
+    lib.tcorr_selftest_timeout.argtypes = [vp]
+    lib.tcorr_selftest_timeout.restype = ci
     lib.tcorr_status_poll.argtypes = [vp]
     lib.tcorr_status_poll.restype = ci
     lib.tcorr_strerror.argtypes = [ci]
@@ -229,6 +231,13 @@ def tcorr_profile_read(kind: int):
 
 def tcorr_status_poll(stream=None) -> int:
     return int(load().tcorr_status_poll(_stream_ptr(stream)))
+
+
+def tcorr_selftest_timeout(stream=None) -> None:
+    """Enqueue the device-side timeout self-test (sets TCORR_ETIMEOUT in the status word)."""
+    rc = load().tcorr_selftest_timeout(_stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_selftest_timeout")
 
 
 def tcorr_version() -> int:

@@ -151,3 +151,13 @@ def test_profile_hooks_time_the_dominant_kernel(T):
     T.tcorr_msd(x, 300, 1, "plain")
     assert n0 == 3 and n1 == 1 and ms0 > 0 and ms1 > 0
     assert T.tcorr_profile_read(0) == (0.0, 0)
+
+
+def test_device_timeout_sets_status_word_and_context_survives(T):
+    assert T.tcorr_status_poll() == 0
+    T.tcorr_selftest_timeout()
+    assert T.tcorr_status_poll() == 6          # TCORR_ETIMEOUT, reported once
+    assert T.tcorr_status_poll() == 0          # and cleared
+    x = dev(synth.random_walk_positions(300, 20, 0.01, 3.0, seed=13))
+    m = T.tcorr_msd(x, 100, 1, "fp16x3").cpu().numpy()   # the context is still usable
+    assert m[0] == 0.0 and np.all(np.isfinite(m))
