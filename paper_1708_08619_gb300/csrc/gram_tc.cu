@@ -329,7 +329,7 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
 // Where a work item's instance lives: one instance whose tensor maps and
 // arguments are kernel parameters, or a batch of instances described in
 // device memory (item -> instance by binary search over item offsets).
-struct alignas(64) InstDesc {
+struct InstDesc {                // CUtensorMap members keep it 64-byte aligned
     CUtensorMap maps[4];      // A hi, A lo, B hi, B lo
     GramArgs ga;
     int64_t item_begin;       // first global work item of this instance
@@ -340,11 +340,6 @@ struct SrcSingle {
     const GramArgs *a;
     __device__ __forceinline__ int64_t n_items() const { return a->n_items; }
     __device__ __forceinline__ unsigned long long *counter() const { return a->counter; }
-    __device__ __forceinline__ const GramArgs *get(int64_t item, int64_t &local, const CUtensorMap *const *&maps) const {
-        local = item;
-        maps = m;
-        return a;
-    }
 };
 
 struct SrcBatch {
@@ -964,10 +959,10 @@ __device__ __forceinline__ float poly_value(const PolyPrepArgs &a, int64_t j, in
 
 // One block per (copy r, phase row j): row max (FP16 scale), then hi/lo.
 template <int PREC>
-__global__ void __launch_bounds__(PREP_THREADS) poly_split_kernel(const __grid_constant__ PolyPrepArgs a) {
+__device__ __forceinline__ void poly_split_body(const PolyPrepArgs &a, int64_t blk) {
     __shared__ float red_f[PREP_THREADS / 32];
-    const int64_t j = blockIdx.x % POLY_L;
-    const int64_t r = blockIdx.x / POLY_L;
+    const int64_t j = blk % POLY_L;
+    const int64_t r = blk / POLY_L;
     const int tid = threadIdx.x;
     float scale = 1.f;
     if (PREC == P_FP16) {
@@ -999,6 +994,21 @@ __global__ void __launch_bounds__(PREP_THREADS) poly_split_kernel(const __grid_c
     }
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(PREP_THREADS) poly_split_kernel(const __grid_constant__ PolyPrepArgs a) {
+    poly_split_body<PREC>(a, blockIdx.x);
+}
+
+// Batch: 8 x L blocks per instance; block -> instance by binary search.
+template <int PREC>
+__global__ void __launch_bounds__(PREP_THREADS) poly_split_batch_kernel(const PolyPrepArgs *__restrict__ d, int n) {
+    const int64_t b = blockIdx.x;
+    const int64_t per = 8 * POLY_L;
+    const int i = static_cast<int>(b / per);
+    if (i >= n) return;
+    poly_split_body<PREC>(d[i], b - static_cast<int64_t>(i) * per);
+}
+
 // S(t) = |x_t|^2 (FP64) for the polyphase MSD: one thread per frame.
 __global__ void poly_s_kernel(const float *X, int64_t T, int64_t K, double *S) {
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1017,13 +1027,11 @@ struct PolyReduceArgs {
     int kind;
     const double *S_prefix;          // kind 0: prefix sums of S, T+1 entries
     double *out;
+    int64_t lag_begin;               // batch: first global lag of this instance
 };
 
 // One warp per lag: the blocks (g, q, h, c) whose window holds tau.
-__global__ void poly_reduce_kernel(const __grid_constant__ PolyReduceArgs a) {
-    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (tau > a.tau_max) return;
+__device__ __forceinline__ void poly_reduce_body(const PolyReduceArgs &a, int64_t tau, int lane) {
     double sum = 0.0;
     const int64_t nterm = a.n_groups * 6 * 2;     // (g, h, c, q candidate)
     for (int64_t tt = lane; tt < nterm; tt += 32) {
@@ -1056,6 +1064,24 @@ __global__ void poly_reduce_kernel(const __grid_constant__ PolyReduceArgs a) {
         }
         a.out[tau] = v;
     }
+}
+
+__global__ void poly_reduce_kernel(const __grid_constant__ PolyReduceArgs a) {
+    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (tau > a.tau_max) return;
+    poly_reduce_body(a, tau, threadIdx.x & 31);
+}
+
+__global__ void poly_reduce_batch_kernel(const PolyReduceArgs *__restrict__ d, int n, int64_t total) {
+    const int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (g >= total) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].lag_begin <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    poly_reduce_body(d[lo], g - d[lo].lag_begin, threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------ host
@@ -1352,6 +1378,7 @@ struct BatchLayout {
     std::vector<GramLayout> L;
     std::vector<size_t> base;
     size_t off_inst = 0, off_split = 0, off_pfx = 0, off_red = 0, off_counter = 0, total = 0;
+    size_t off_pprep = 0, off_pred = 0;
     int64_t total_items = 0, total_frames = 0, total_pfx = 0, total_lags = 0;
 };
 
@@ -1381,6 +1408,8 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     B->off_pfx = take(sizeof(PfxDesc) * (B->n_msd > 0 ? B->n_msd : 1));
     B->off_red = take(sizeof(LagReduceDesc) * count);
     B->off_counter = take(sizeof(unsigned long long));
+    B->off_pprep = take(sizeof(PolyPrepArgs) * count);
+    B->off_pred = take(sizeof(PolyReduceArgs) * count);
     B->base.resize(count);
     for (int k = 0; k < count; ++k) {
         const int i = B->order[k];
@@ -1395,12 +1424,17 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     return B->total_frames < (int64_t(1) << 31) && B->total_items < (int64_t(1) << 40);
 }
 
-// Enqueues one polyphase instance: operand copies, S(t) and its prefix sums
-// (MSD), the Gram kernel over (q, h, c) blocks, and the lag reduction.
-int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, int num_sms,
-             cudaStream_t st) {
+// Host-side description of one polyphase instance: prep arguments, the Gram
+// kernel's tensor maps and arguments, and the reduction arguments.
+struct PolySetup {
+    PolyPrepArgs prep;
+    InstDesc gram;
+    PolyReduceArgs red;
+};
+
+int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, PolySetup *P) {
     const int64_t T = L.p.T, N = L.p.N;
-    PolyPrepArgs pa;
+    PolyPrepArgs &pa = P->prep;
     pa.X = d_x;
     pa.T = T;
     pa.K = 3 * N;
@@ -1412,27 +1446,12 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
     pa.Yl = base + L.off_xl;
     pa.inv_scale = reinterpret_cast<float *>(base + L.off_scale);
     pa.kind = kind;
-    const unsigned g = 8 * POLY_L;
-    switch (L.prec) {
-        case P_FP16: poly_split_kernel<P_FP16><<<g, PREP_THREADS, 0, st>>>(pa); break;
-        case P_BF16: poly_split_kernel<P_BF16><<<g, PREP_THREADS, 0, st>>>(pa); break;
-        default: poly_split_kernel<P_TF32><<<g, PREP_THREADS, 0, st>>>(pa); break;
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "poly_split_kernel launch");
-    double *S = reinterpret_cast<double *>(base + L.off_S);
-    double *prefix = reinterpret_cast<double *>(base + L.off_prefix);
-    if (kind == 0) {
-        poly_s_kernel<<<static_cast<unsigned>(ceil_div(T, 256)), 256, 0, st>>>(d_x, T, 3 * N, S);
-        s_prefix_kernel<<<1, PFX_THREADS, 0, st>>>(S, T, 1, T + 1, prefix);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly S launch");
-    }
     EncodeFn encode = get_encode();
     if (!encode) return TCORR_EUNSUPPORTED;
     const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    CUtensorMap maps[4];
+    CUtensorMap *maps = P->gram.maps;
     void *bases[2] = {base + L.off_xh, base + L.off_xl};
     const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kalloc * L.esize);
     for (int h = 0; h < 2; ++h) {
@@ -1453,7 +1472,8 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase B)");
     }
-    GramArgs ga{};
+    GramArgs &ga = P->gram.ga;
+    ga = GramArgs{};
     ga.T = T;
     ga.s = 1;
     ga.tau_max = L.p.tau_max;
@@ -1471,17 +1491,8 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
     ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
     ga.mode = 1;
     ga.nq = L.nq;
-    if ((e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
-        return cuda_fail(e, "work-item counter reset");
-    const int grid = static_cast<int>(ga.n_items < num_sms ? ga.n_items : num_sms);
-    switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
-        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st, kind); break;
-        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st, kind); break;
-        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st, kind); break;
-        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st, kind); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel (polyphase) launch");
-    PolyReduceArgs ra;
+    P->gram.item_begin = 0;
+    PolyReduceArgs &ra = P->red;
     ra.partial = ga.partial;
     ra.T = T;
     ra.N = N;
@@ -1489,9 +1500,50 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
     ra.nq = L.nq;
     ra.n_groups = L.p.n_groups;
     ra.kind = kind;
-    ra.S_prefix = kind == 0 ? prefix : nullptr;
+    ra.S_prefix = kind == 0 ? reinterpret_cast<const double *>(base + L.off_prefix) : nullptr;
     ra.out = d_out;
-    poly_reduce_kernel<<<static_cast<unsigned>(ceil_div((L.p.tau_max + 1) * 32, 256)), 256, 0, st>>>(ra);
+    ra.lag_begin = 0;
+    return TCORR_OK;
+}
+
+// S(t) and its prefix sums for a polyphase MSD instance.
+cudaError_t poly_msd_s(const float *d_x, const GramLayout &L, uint8_t *base, cudaStream_t st) {
+    const int64_t T = L.p.T;
+    double *S = reinterpret_cast<double *>(base + L.off_S);
+    double *prefix = reinterpret_cast<double *>(base + L.off_prefix);
+    poly_s_kernel<<<static_cast<unsigned>(ceil_div(T, 256)), 256, 0, st>>>(d_x, T, 3 * L.p.N, S);
+    s_prefix_kernel<<<1, PFX_THREADS, 0, st>>>(S, T, 1, T + 1, prefix);
+    return cudaGetLastError();
+}
+
+// Enqueues one polyphase instance: operand copies, S(t) and its prefix sums
+// (MSD), the Gram kernel over (q, h, c) blocks, and the lag reduction.
+int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, int num_sms,
+             cudaStream_t st) {
+    PolySetup P;
+    int rc = poly_setup(kind, d_x, L, base, d_out, &P);
+    if (rc != TCORR_OK) return rc;
+    const unsigned g = 8 * POLY_L;
+    switch (L.prec) {
+        case P_FP16: poly_split_kernel<P_FP16><<<g, PREP_THREADS, 0, st>>>(P.prep); break;
+        case P_BF16: poly_split_kernel<P_BF16><<<g, PREP_THREADS, 0, st>>>(P.prep); break;
+        default: poly_split_kernel<P_TF32><<<g, PREP_THREADS, 0, st>>>(P.prep); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "poly_split_kernel launch");
+    if (kind == 0 && (e = poly_msd_s(d_x, L, base, st)) != cudaSuccess) return cuda_fail(e, "poly S launch");
+    const GramArgs &ga = P.gram.ga;
+    if ((e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_fail(e, "work-item counter reset");
+    const int grid = static_cast<int>(ga.n_items < num_sms ? ga.n_items : num_sms);
+    switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(P.gram.maps, ga, grid, st, kind); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(P.gram.maps, ga, grid, st, kind); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(P.gram.maps, ga, grid, st, kind); break;
+        default: e = launch_gram<P_TF32, false>(P.gram.maps, ga, grid, st, kind); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel (polyphase) launch");
+    poly_reduce_kernel<<<static_cast<unsigned>(ceil_div((L.p.tau_max + 1) * 32, 256)), 256, 0, st>>>(P.red);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_reduce launch");
     return TCORR_OK;
 }
@@ -1659,7 +1711,10 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     std::vector<LagReduceDesc> red(count);
     std::vector<InstDesc> big_desc;
     int64_t item_begin = 0, frame_begin = 0, pfx_begin = 0, lag_begin = 0;
-    std::vector<int> poly;
+    std::vector<PolyPrepArgs> pprep;
+    std::vector<PolyReduceArgs> pred;
+    std::vector<int> poly_msd;
+    int64_t plag_begin = 0;
     int nb = 0;                          // band instances, in descriptor order
     for (int k = 0; k < count; ++k) {
         const int i = B.order[k];
@@ -1667,7 +1722,21 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         const GramLayout &L = B.L[i];
         uint8_t *base = ws + B.base[i];
         if (L.poly) {
-            poly.push_back(i);
+            PolySetup P;
+            const int rc = poly_setup(it.kind, it.d_x, L, base, it.d_out, &P);
+            if (rc != TCORR_OK) return rc;
+            if (L.p.n_items >= big_items) {
+                big_desc.push_back(P.gram);
+            } else {
+                P.gram.item_begin = item_begin;
+                item_begin += L.p.n_items;
+                inst.push_back(P.gram);
+            }
+            pprep.push_back(P.prep);
+            P.red.lag_begin = plag_begin;
+            plag_begin += it.tau_max + 1;
+            pred.push_back(P.red);
+            if (it.kind == 0) poly_msd.push_back(i);
             continue;
         }
         InstDesc d;
@@ -1699,22 +1768,33 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         lag_begin += it.tau_max + 1;
         ++nb;
     }
-    for (int i : poly) {
-        const int rc = poly_run(items[i].kind, items[i].d_x, B.L[i], ws + B.base[i], items[i].d_out, num_sms, st);
-        if (rc != TCORR_OK) return rc;
-    }
-    if (nb == 0) return TCORR_OK;
-    cudaError_t e;
+    const int np = static_cast<int>(pprep.size());
+    cudaError_t e = cudaSuccess;
     if ((!inst.empty() &&
          (e = upload_bytes(ws + B.off_inst, inst.data(), sizeof(InstDesc) * inst.size(), st)) != cudaSuccess) ||
-        (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * nb, st)) != cudaSuccess ||
-        (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * nb, st)) != cudaSuccess ||
-        (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx, pfx.data(), sizeof(PfxDesc) * pfx.size(), st)) != cudaSuccess))
+        (nb > 0 && (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * nb, st)) != cudaSuccess) ||
+        (nb > 0 && (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * nb, st)) != cudaSuccess) ||
+        (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx, pfx.data(), sizeof(PfxDesc) * pfx.size(), st)) != cudaSuccess) ||
+        (np > 0 && (e = upload_bytes(ws + B.off_pprep, pprep.data(), sizeof(PolyPrepArgs) * np, st)) != cudaSuccess) ||
+        (np > 0 && (e = upload_bytes(ws + B.off_pred, pred.data(), sizeof(PolyReduceArgs) * np, st)) != cudaSuccess))
         return cuda_fail(e, "descriptor upload");
+    if (np > 0) {
+        const PolyPrepArgs *d_pp = reinterpret_cast<const PolyPrepArgs *>(ws + B.off_pprep);
+        const unsigned gp = static_cast<unsigned>(np) * 8u * POLY_L;
+        switch (B.prec) {
+            case P_FP16: poly_split_batch_kernel<P_FP16><<<gp, PREP_THREADS, 0, st>>>(d_pp, np); break;
+            case P_BF16: poly_split_batch_kernel<P_BF16><<<gp, PREP_THREADS, 0, st>>>(d_pp, np); break;
+            default: poly_split_batch_kernel<P_TF32><<<gp, PREP_THREADS, 0, st>>>(d_pp, np); break;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_split_batch_kernel launch");
+        for (int i : poly_msd)
+            if ((e = poly_msd_s(items[i].d_x, B.L[i], ws + B.base[i], st)) != cudaSuccess)
+                return cuda_fail(e, "poly S launch");
+    }
 
     const SplitDesc *d_spl = reinterpret_cast<const SplitDesc *>(ws + B.off_split);
     const unsigned gs = static_cast<unsigned>(B.total_frames);
-    switch (B.prec) {
+    if (nb > 0) switch (B.prec) {
         case P_FP16: split_batch_kernel<P_FP16><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
         case P_BF16: split_batch_kernel<P_BF16><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
         default: split_batch_kernel<P_TF32><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
@@ -1754,8 +1834,15 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         }
         if (e != cudaSuccess) return cuda_fail(e, "gram_band_batch_kernel launch");
     }
-    e = launch_lag_reduce_batch(reinterpret_cast<const LagReduceDesc *>(ws + B.off_red), nb, B.total_lags, st);
-    if (e != cudaSuccess) return cuda_fail(e, "lag_reduce_batch launch");
+    if (nb > 0) {
+        e = launch_lag_reduce_batch(reinterpret_cast<const LagReduceDesc *>(ws + B.off_red), nb, B.total_lags, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lag_reduce_batch launch");
+    }
+    if (np > 0) {
+        poly_reduce_batch_kernel<<<static_cast<unsigned>(ceil_div(plag_begin * 32, 256)), 256, 0, st>>>(
+            reinterpret_cast<const PolyReduceArgs *>(ws + B.off_pred), np, plag_begin);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_reduce_batch launch");
+    }
     return TCORR_OK;
 }
 
@@ -1766,12 +1853,10 @@ namespace {
 // word records TCORR_ETIMEOUT, and the kernel returns normally.
 __global__ void timeout_probe_kernel(unsigned long long limit_ns) {
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int abort_flag;
     if (threadIdx.x != 0) return;
     const uint32_t b = smem_u32(&bar);
     mbar_init(b, 1);
     fence_barrier_init();
-    abort_flag = 0;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(b, 0u)) return;              // never: nobody arrives
