@@ -57,12 +57,27 @@ WORKLOADS = {
 
 
 def issued_over_useful(N, T, tau_max, s, BO=128, BF=192):
-    """Tile entries computed by the band kernel per useful (origin, lag) pair."""
-    n_orig = (T - 1) // s + 1
-    n_rows = -(-n_orig // BO)
-    n_cols = -(-(BO + tau_max // s) // BF)
-    useful = updates(1, T, tau_max, s)
-    return n_rows * n_cols * BO * BF * min(s, tau_max + 1) / useful
+    """Tile entries the band kernel issues per useful (origin, lag) pair.
+
+    Per residue rho of the stride: row tiles of BO origins times column tiles
+    of BF frames; a column tile is issued ncol = min(BF, m_max - c*BF + BO)
+    columns wide (rounded up to 16), tiles past the band or past the last
+    frame are skipped."""
+    issued = 0
+    for rho in range(min(s, tau_max + 1)):
+        m_max = (tau_max - rho) // s
+        n_rho = (T - 1 - rho) // s + 1
+        n_orig = (T - 1) // s + 1
+        n_rows = -(-n_orig // BO)
+        n_cols = -(-(BO + tau_max // s) // BF)
+        for r in range(n_rows):
+            for c in range(n_cols):
+                if c * BF - BO + 1 > m_max or r * BO + c * BF >= n_rho:
+                    continue
+                need = m_max - c * BF + BO
+                ncol = BF if need >= BF else max(16, -(-need // 16) * 16)
+                issued += BO * ncol
+    return issued / updates(1, T, tau_max, s)
 
 
 def updates(N, T, tau_max, s):

@@ -62,6 +62,10 @@ constexpr int ROWB = 64;            // bytes of K per staged row = one 64B swizz
 constexpr int A_BYTES = BO * ROWB;  // 8 KB
 constexpr int B_BYTES = BF * ROWB;  // 12 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int NBOX = 32;            // B rows per box of the narrow-tile maps (full tiles: one BF box)
+constexpr int NBOX_BYTES = NBOX * ROWB;
+static_assert(BF % NBOX == 0, "a narrow B tile is a whole number of boxes");
+constexpr int NMAPS = 6;            // A hi, A lo, B hi, B lo, then B hi / lo with NBOX-row boxes
 constexpr int WPG = 320;            // window width per item (>= BO + BF - 1 = 319)
 constexpr int NTHREADS = 320;   // 10 warps
 constexpr int NEPI = 8;          // epilogue warps
@@ -268,12 +272,22 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 // (b_x: extra K offset; b_z: shifted operand copy, polyphase only).  Entry
 // (row i, column j) of the tile holds band offset / lag m = moff + j - i,
 // kept if 0 <= m <= m_max.  The per-row FP16 scale of row i is
-// inv_scale[sa0 + i*sstr] and of column j inv_scale[sb0 + j*sstr].
+// inv_scale[sa0 + i*sstr] and of column j inv_scale[sb0 + j*sstr].  Only
+// columns j < ncol can hold a kept lag (m_max - moff + BO of them, rounded
+// up to the MMA's N granularity of 16): the last column tile of a band row
+// is issued that narrow.
 struct Item {
     int64_t rho, a_y, b_x, b_y, b_z, moff, m_max, kb0, kb1;
     int64_t sa0, sb0, sstr, a_rows;   // a_rows: A rows that hold data (scale lookups)
+    int ncol;
     bool empty;
 };
+
+__device__ __forceinline__ int item_ncol(int64_t moff, int64_t m_max) {
+    const int64_t need = m_max - moff + BO;
+    if (need >= BF) return BF;
+    return need <= 16 ? 16 : static_cast<int>((need + 15) & ~int64_t(15));
+}
 
 __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
     Item I;
@@ -300,6 +314,7 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
         I.kb0 = g * a.kb_per_item;
         I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
         I.empty = (c * BF - BO + 1 > I.m_max) || (k0 >= n_rho) || (I.kb0 >= I.kb1);
+        I.ncol = item_ncol(I.moff, I.m_max);
     } else {
         // polyphase block (q, h, c) of M_q = sum_p Y[.][p] Y[.][p+q]^T, rows = phases
         const int64_t c = t % 2;
@@ -322,6 +337,7 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
         I.kb0 = g * a.kb_per_item;
         I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
         I.empty = (I.moff + BF - 1 < 0) || (I.moff - (BO - 1) > a.tau_max) || (I.kb0 >= I.kb1);
+        I.ncol = item_ncol(I.moff, I.m_max);
     }
     return I;
 }
@@ -330,13 +346,13 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
 // arguments are kernel parameters, or a batch of instances described in
 // device memory (item -> instance by binary search over item offsets).
 struct InstDesc {                // CUtensorMap members keep it 64-byte aligned
-    CUtensorMap maps[4];      // A hi, A lo, B hi, B lo
+    CUtensorMap maps[NMAPS];  // A hi, A lo, B hi, B lo, narrow B hi, narrow B lo
     GramArgs ga;
     int64_t item_begin;       // first global work item of this instance
 };
 
 struct SrcSingle {
-    const CUtensorMap *m[4];
+    const CUtensorMap *m[NMAPS];
     const GramArgs *a;
     __device__ __forceinline__ int64_t n_items() const { return a->n_items; }
     __device__ __forceinline__ unsigned long long *counter() const { return a->counter; }
@@ -364,16 +380,16 @@ struct SrcBatch {
 
 // Resolve an item to (its instance's arguments, its four tensor maps, local index).
 __device__ __forceinline__ const GramArgs *resolve(const SrcSingle &src, int64_t item, int64_t &local,
-                                                   const CUtensorMap *(&maps)[4]) {
+                                                   const CUtensorMap *(&maps)[NMAPS]) {
     local = item;
-    for (int i = 0; i < 4; ++i) maps[i] = src.m[i];
+    for (int i = 0; i < NMAPS; ++i) maps[i] = src.m[i];
     return src.a;
 }
 __device__ __forceinline__ const GramArgs *resolve(const SrcBatch &src, int64_t item, int64_t &local,
-                                                   const CUtensorMap *(&maps)[4]) {
+                                                   const CUtensorMap *(&maps)[NMAPS]) {
     const CUtensorMap *m0;
     const GramArgs *a = src.get(item, local, m0);
-    for (int i = 0; i < 4; ++i) maps[i] = m0 + i;
+    for (int i = 0; i < NMAPS; ++i) maps[i] = m0 + i;
     return a;
 }
 
@@ -450,33 +466,43 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             mbar_arrive(iq_full_bar(qs));
             if (item < 0) break;
             int64_t local;
-            const CUtensorMap *mp[4];
+            const CUtensorMap *mp[NMAPS];
             const GramArgs &a = *resolve(src, item, local, mp);
             const Item I = decode_item(a, local);
             if (I.empty) continue;
             if (mp[0] != last_map) {      // new instance: bring its descriptors close to the TMA unit
-                for (int i = 0; i < 4; ++i) prefetch_tensormap(mp[i]);
+                for (int i = 0; i < NMAPS; ++i) prefetch_tensormap(mp[i]);
                 last_map = mp[0];
             }
             const int b3d = a.b3d;
             const int32_t ay = static_cast<int32_t>(I.a_y), by = static_cast<int32_t>(I.b_y);
             const int32_t bz = static_cast<int32_t>(I.b_z), bx = static_cast<int32_t>(I.b_x);
+            // a full tile loads B as one BF-row box; a narrow one only the NBOX-row boxes it uses
+            const bool narrow = I.ncol < BF;
+            const int nbox = narrow ? (I.ncol + NBOX - 1) / NBOX : 1;
+            const CUtensorMap *mbh = narrow ? mp[4] : mp[2], *mbl = narrow ? mp[5] : mp[3];
+            const int32_t brows = narrow ? NBOX : BF;
+            const uint32_t stage_tx = 2 * A_BYTES + 2 * nbox * brows * ROWB;
             for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
                 if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
-                mbar_arrive_expect_tx(full_bar(st), STAGE_BYTES);
+                mbar_arrive_expect_tx(full_bar(st), stage_tx);
                 const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
                 const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
                 tma_load_2d(sbase, mp[0], kx, ay, full_bar(st));
                 tma_load_2d(sbase + A_BYTES, mp[1], kx, ay, full_bar(st));
-                if (b3d == 2) {          // polyphase: (K + aligned shift, phase row, shifted copy)
-                    tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx + bx, by, bz, full_bar(st));
-                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx + bx, by, bz, full_bar(st));
-                } else if (b3d) {        // band, stride > 1: (K, residue, frame index)
-                    tma_load_3d(sbase + 2 * A_BYTES, mp[2], kx, bz, by, full_bar(st));
-                    tma_load_3d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, bz, by, full_bar(st));
-                } else {
-                    tma_load_2d(sbase + 2 * A_BYTES, mp[2], kx, by, full_bar(st));
-                    tma_load_2d(sbase + 2 * A_BYTES + B_BYTES, mp[3], kx, by, full_bar(st));
+                for (int j = 0; j < nbox; ++j) {
+                    const uint32_t sh = sbase + 2 * A_BYTES + j * NBOX_BYTES, sl = sh + B_BYTES;
+                    const int32_t byj = by + j * NBOX;
+                    if (b3d == 2) {      // polyphase: (K + aligned shift, phase row, shifted copy)
+                        tma_load_3d(sh, mbh, kx + bx, byj, bz, full_bar(st));
+                        tma_load_3d(sl, mbl, kx + bx, byj, bz, full_bar(st));
+                    } else if (b3d) {    // band, stride > 1: (K, residue, frame index)
+                        tma_load_3d(sh, mbh, kx, bz, byj, full_bar(st));
+                        tma_load_3d(sl, mbl, kx, bz, byj, full_bar(st));
+                    } else {
+                        tma_load_2d(sh, mbh, kx, byj, full_bar(st));
+                        tma_load_2d(sl, mbl, kx, byj, full_bar(st));
+                    }
                 }
                 if (++st == STAGES) {
                     st = 0;
@@ -498,10 +524,11 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             mbar_arrive(iq_empty_bar(qs));
             if (item < 0) break;
             int64_t local;
-            const CUtensorMap *mp[4];
+            const CUtensorMap *mp[NMAPS];
             const GramArgs &a = *resolve(src, item, local, mp);
             const Item I = decode_item(a, local);
             if (I.empty) continue;
+            const uint32_t idesc_i = (idesc & ~(0x3Fu << 17)) | (static_cast<uint32_t>(I.ncol >> 3) << 17);
             const int64_t sub_kb = a.sub_kb;
             for (int64_t kc = I.kb0; kc < I.kb1 && !aborted; kc += sub_kb) {
                 const int64_t kc1 = min(I.kb1, kc + sub_kb);
@@ -527,10 +554,10 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint64_t adv = static_cast<uint64_t>(ks * 2);   // 32 bytes of K in 16-byte units
                         const uint32_t acc = (kb != kc || ks != 0) ? 1u : 0u;
-                        tc_mma<PREC>(d, dAh + adv, dBh + adv, idesc, acc);
-                        tc_mma<PREC>(d, dAh + adv, dBl + adv, idesc, 1u);
-                        tc_mma<PREC>(d, dAl + adv, dBh + adv, idesc, 1u);
-                        if (X4) tc_mma<PREC>(d, dAl + adv, dBl + adv, idesc, 1u);
+                        tc_mma<PREC>(d, dAh + adv, dBh + adv, idesc_i, acc);
+                        tc_mma<PREC>(d, dAh + adv, dBl + adv, idesc_i, 1u);
+                        tc_mma<PREC>(d, dAl + adv, dBh + adv, idesc_i, 1u);
+                        if (X4) tc_mma<PREC>(d, dAl + adv, dBl + adv, idesc_i, 1u);
                     }
                     issued = true;
                     tc_commit(empty_bar(st));
@@ -567,9 +594,10 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             if (lane == 0) mbar_arrive(iq_empty_bar(qs));
             if (item < 0) break;
             int64_t local;
-            const CUtensorMap *mp[4];
+            const CUtensorMap *mp[NMAPS];
             const GramArgs &a = *resolve(src, item, local, mp);
             int64_t kb0, kb1;
+            int ncol;
             {
                 const Item I0 = decode_item(a, local);
                 if (I0.empty) {
@@ -579,7 +607,10 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 }
                 kb0 = I0.kb0;
                 kb1 = I0.kb1;
+                ncol = I0.ncol;
             }
+            // columns of this warp's half that the MMA wrote (the rest is stale and masked)
+            const int hcols = ncol - (BF / 2) * half;
             const int64_t sub_kb = a.sub_kb;
             float acc2[BF / 2];
 #pragma unroll
@@ -593,13 +624,13 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + (static_cast<uint32_t>(32 * q) << 16) +
                                        static_cast<uint32_t>(b * BF + (BF / 2) * half);
-                {
+                if (hcols > 0) {
                     uint32_t v[64];
                     tmem_ld64(tbase, v);
 #pragma unroll
                     for (int jj = 0; jj < 64; ++jj) acc2[jj] += __uint_as_float(v[jj]);
                 }
-                {
+                if (hcols > 64) {
                     uint32_t v[32];
                     tmem_ld32(tbase + 64, v);
 #pragma unroll
@@ -661,12 +692,15 @@ template <int PREC, bool X4>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gram_band_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                     const __grid_constant__ CUtensorMap tmBhn, const __grid_constant__ CUtensorMap tmBln,
                      const __grid_constant__ GramArgs a) {
     SrcSingle src;
     src.m[0] = &tmAh;
     src.m[1] = &tmAl;
     src.m[2] = &tmBh;
     src.m[3] = &tmBl;
+    src.m[4] = &tmBhn;
+    src.m[5] = &tmBln;
     src.a = &a;
     gram_body<PREC, X4>(src);
 }
@@ -945,68 +979,141 @@ struct PolyPrepArgs {
     int64_t T, K, P, Pp, Kprime, Kalloc;
     void *Yh, *Yl;                   // [8][L][Kalloc]
     float *inv_scale;                // [L]
+    unsigned *rowmax;                // [L] FP16: bits of the largest |value| per phase row (zeroed first)
     int kind;
+    int64_t rm_begin, tile_begin;    // batch: first row-max block / prep tile of this instance
 };
 
-__device__ __forceinline__ float poly_value(const PolyPrepArgs &a, int64_t j, int64_t kk) {
-    if (kk >= a.Kprime) return 0.f;
-    const int64_t ser = kk / a.Pp, p = kk - ser * a.Pp;
-    const int64_t t = p * POLY_L + j;
-    if (p >= a.P || t >= a.T) return 0.f;
-    const float v = a.X[t * a.K + ser];
-    return a.kind == 0 ? v - a.X[ser] : v;
+constexpr int RM_P = 16;                          // frame blocks p per row-max block
+constexpr int PT_K = 32;                          // contraction columns per prep tile
+constexpr int PT_ROWS = PT_K + 7;                 // + the largest copy shift
+constexpr int PT_LD = POLY_L + 1;                 // shared row stride (floats), conflict-free reads
+constexpr size_t PT_SMEM = size_t(PT_ROWS) * PT_LD * sizeof(float) + POLY_L * sizeof(float) +
+                           2 * PT_ROWS * sizeof(int);
+static_assert(POLY_L > PREP_THREADS && POLY_L <= 2 * PREP_THREADS, "two phases per prep thread");
+
+__host__ __device__ __forceinline__ int64_t poly_rm_blocks(int64_t P) { return (P + RM_P - 1) / RM_P; }
+__host__ __device__ __forceinline__ int64_t poly_tiles(int64_t Kalloc) { return Kalloc / PT_K; }
+
+// FP16 only: largest |value| of each phase row j over all series and frame
+// blocks, one block per RM_P frame blocks (384 threads, one per phase, reads
+// consecutive frames), folded into rowmax[] with an unsigned max on the bit
+// pattern (order-preserving for non-negative floats).
+__device__ __forceinline__ void poly_rowmax_body(const PolyPrepArgs &a, int64_t blk) {
+    const int j = threadIdx.x;
+    const int64_t p0 = blk * RM_P;
+    float mx = 0.f;
+#pragma unroll 4
+    for (int dp = 0; dp < RM_P; ++dp) {
+        const int64_t t = (p0 + dp) * POLY_L + j;
+        if (p0 + dp >= a.P || t >= a.T) break;
+        for (int64_t ser = 0; ser < a.K; ++ser) {
+            const float v = a.X[t * a.K + ser];
+            mx = fmaxf(mx, fabsf(a.kind == 0 ? v - a.X[ser] : v));
+        }
+    }
+    if (mx > 0.f) atomicMax(a.rowmax + j, __float_as_uint(mx));
 }
 
-// One block per (copy r, phase row j): row max (FP16 scale), then hi/lo.
-template <int PREC>
-__device__ __forceinline__ void poly_split_body(const PolyPrepArgs &a, int64_t blk) {
-    __shared__ float red_f[PREP_THREADS / 32];
-    const int64_t j = blk % POLY_L;
-    const int64_t r = blk / POLY_L;
-    const int tid = threadIdx.x;
-    float scale = 1.f;
-    if (PREC == P_FP16) {
-        float mx = 0.f;
-        for (int64_t kk = tid; kk < a.Kprime; kk += PREP_THREADS) mx = fmaxf(mx, fabsf(poly_value(a, j, kk)));
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if ((tid & 31) == 0) red_f[tid >> 5] = mx;
-        __syncthreads();
-        mx = red_f[0];
-#pragma unroll
-        for (int i = 1; i < PREP_THREADS / 32; ++i) mx = fmaxf(mx, red_f[i]);
-        int e = 0;
-        if (mx > 0.f) {
-            int ex;
-            frexpf(mx, &ex);
-            e = 14 - ex;
-            e = e < -60 ? -60 : (e > 60 ? 60 : e);
-        }
-        scale = ldexpf(1.f, e);
-        if (tid == 0 && r == 0) a.inv_scale[j] = ldexpf(1.f, -e);
+__global__ void __launch_bounds__(POLY_L) poly_rowmax_kernel(const __grid_constant__ PolyPrepArgs a) {
+    poly_rowmax_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(POLY_L) poly_rowmax_batch_kernel(const PolyPrepArgs *__restrict__ d, int n) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].rm_begin <= b) lo = mid;
+        else hi = mid - 1;
     }
-    const int64_t rowoff = (r * POLY_L + j) * a.Kalloc;
-    for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < a.Kalloc; k0 += PREP_THREADS * 8) {
+    poly_rowmax_body(d[lo], b - d[lo].rm_begin);
+}
+
+// One block per tile of PT_K contraction columns [k0, k0 + PT_K): stages the
+// values of columns k0 .. k0 + PT_K + 6 for all 384 phases in shared memory
+// (reads along phases, i.e. consecutive frames), then writes the 8 copies
+// Y_r[j][k] = value(j, k + r) as hi/lo pairs, 8 consecutive k per thread.
+template <int PREC>
+__device__ __forceinline__ void poly_split_body(const PolyPrepArgs &a, int64_t tile, float *sm) {
+    float *V = sm;                                   // [PT_ROWS][PT_LD]
+    float *sc = sm + PT_ROWS * PT_LD;                // [L] per-row scale
+    int *rser = reinterpret_cast<int *>(sc + POLY_L);    // [PT_ROWS] series of column k0 + row
+    int *rp = rser + PT_ROWS;                        // [PT_ROWS] its frame block, -1: zero column
+    const int tid = threadIdx.x;
+    const int k0 = static_cast<int>(tile) * PT_K;
+    if (tid < PT_ROWS) {
+        const int kk = k0 + tid;
+        const int Pp = static_cast<int>(a.Pp);
+        const int ser = kk / Pp, p = kk - ser * Pp;
+        rser[tid] = ser;
+        rp[tid] = (kk < a.Kprime && p < a.P) ? p : -1;
+    }
+    for (int j = tid; j < POLY_L; j += PREP_THREADS) {
+        float s = 1.f;
+        if (PREC == P_FP16) {
+            const float mx = __uint_as_float(a.rowmax[j]);
+            int e = 0;
+            if (mx > 0.f) {
+                int ex;
+                frexpf(mx, &ex);
+                e = 14 - ex;
+                e = e < -60 ? -60 : (e > 60 ? 60 : e);
+            }
+            s = ldexpf(1.f, e);
+            if (tile == 0) a.inv_scale[j] = ldexpf(1.f, -e);
+        }
+        sc[j] = s;
+    }
+    __syncthreads();
+    // phases j = tid and tid + 256 of every staged column: consecutive frames,
+    // independent loads (unrolled) so that many are in flight per thread
+    const bool two = tid < POLY_L - PREP_THREADS;
+#pragma unroll 13
+    for (int row = 0; row < PT_ROWS; ++row) {
+        const int p = rp[row], ser = rser[row];
+        float v0 = 0.f, v1 = 0.f;
+        if (p >= 0) {
+            const int64_t t0 = static_cast<int64_t>(p) * POLY_L + tid;
+            const float ref = a.kind == 0 ? a.X[ser] : 0.f;
+            if (t0 < a.T) v0 = a.X[t0 * a.K + ser] - ref;
+            if (two && t0 + PREP_THREADS < a.T) v1 = a.X[(t0 + PREP_THREADS) * a.K + ser] - ref;
+        }
+        V[row * PT_LD + tid] = v0;
+        if (two) V[row * PT_LD + tid + PREP_THREADS] = v1;
+    }
+    __syncthreads();
+    constexpr int UNITS = 8 * POLY_L * (PT_K / 8);   // (copy r, phase j, octet) -> 8 elements
+    for (int u = tid; u < UNITS; u += PREP_THREADS) {
+        const int oct = u & (PT_K / 8 - 1);
+        const int rj = u / (PT_K / 8);
+        const int r = rj / POLY_L, j = rj - r * POLY_L;
         float x[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = poly_value(a, j, k0 + i + r);
-        split_store8<PREC>(x, scale, a.Yh, a.Yl, rowoff + k0);
+        for (int i = 0; i < 8; ++i) x[i] = V[(oct * 8 + r + i) * PT_LD + j];
+        const int64_t off = (static_cast<int64_t>(r) * POLY_L + j) * a.Kalloc + k0 + oct * 8;
+        split_store8<PREC>(x, sc[j], a.Yh, a.Yl, off);
     }
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(PREP_THREADS) poly_split_kernel(const __grid_constant__ PolyPrepArgs a) {
-    poly_split_body<PREC>(a, blockIdx.x);
+    extern __shared__ __align__(16) float poly_sm[];
+    poly_split_body<PREC>(a, blockIdx.x, poly_sm);
 }
 
-// Batch: 8 x L blocks per instance; block -> instance by binary search.
+// Batch: tiles of all instances in one grid; tile -> instance by binary search.
 template <int PREC>
 __global__ void __launch_bounds__(PREP_THREADS) poly_split_batch_kernel(const PolyPrepArgs *__restrict__ d, int n) {
+    extern __shared__ __align__(16) float poly_sm[];
     const int64_t b = blockIdx.x;
-    const int64_t per = 8 * POLY_L;
-    const int i = static_cast<int>(b / per);
-    if (i >= n) return;
-    poly_split_body<PREC>(d[i], b - static_cast<int64_t>(i) * per);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].tile_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    poly_split_body<PREC>(d[lo], b - d[lo].tile_begin, poly_sm);
 }
 
 // S(t) = |x_t|^2 (FP64) for the polyphase MSD: one thread per frame.
@@ -1030,50 +1137,50 @@ struct PolyReduceArgs {
     int64_t lag_begin;               // batch: first global lag of this instance
 };
 
-// One warp per lag: the blocks (g, q, h, c) whose window holds tau.
-__device__ __forceinline__ void poly_reduce_body(const PolyReduceArgs &a, int64_t tau, int lane) {
+// One thread per lag.  Block (g, q, h, c) holds lag tau at window slot
+// w = tau + 128 h - 192 c + 127 - q L; the window (319 slots) is shorter
+// than L, so for each (g, h, c) only q = floor(base / L) can hold it.  The
+// terms are added in the fixed order g, h, c; neighbouring lags read
+// neighbouring slots.
+__device__ __forceinline__ void poly_reduce_body(const PolyReduceArgs &a, int64_t tau) {
     double sum = 0.0;
-    const int64_t nterm = a.n_groups * 6 * 2;     // (g, h, c, q candidate)
-    for (int64_t tt = lane; tt < nterm; tt += 32) {
-        const int64_t cand = tt % 2;
-        const int64_t hc = (tt / 2) % 6;
-        const int64_t g = tt / 12;
-        const int64_t h = hc / 2, c = hc % 2;
-        const int64_t base = tau + BO * h - BF * c + (BO - 1);     // = q L + w
-        const int64_t q = base / POLY_L - cand;
-        if (q < 0 || q >= a.nq) continue;
-        const int64_t w = base - q * POLY_L;
-        if (w < 0 || w > BO + BF - 2) continue;
-        const int64_t item = ((g * a.nq + q) * 3 + h) * 2 + c;
-        sum += a.partial[item * WPG + w];
-    }
+    const int nq = static_cast<int>(a.nq);
+    for (int64_t g = 0; g < a.n_groups; ++g) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-    if (lane == 0) {
-        const int64_t no = a.T - tau;
-        const double denom = static_cast<double>(a.N) * static_cast<double>(no);
-        double v;
-        if (a.kind == 1) {
-            v = sum / denom;
-        } else if (tau == 0) {
-            v = 0.0;
-        } else {
-            const double P = a.S_prefix[no];
-            const double Q = a.S_prefix[a.T] - a.S_prefix[tau];
-            v = (P + Q - 2.0 * sum) / denom;
+        for (int hc = 0; hc < 6; ++hc) {
+            const int h = hc >> 1, c = hc & 1;
+            const int base = static_cast<int>(tau) + BO * h - BF * c + (BO - 1);
+            if (base < 0) continue;
+            const int q = base / POLY_L;
+            const int w = base - q * POLY_L;
+            if (q >= nq || w > BO + BF - 2) continue;
+            const int64_t item = ((g * nq + q) * 3 + h) * 2 + c;
+            sum += a.partial[item * WPG + w];
         }
-        a.out[tau] = v;
     }
+    const int64_t no = a.T - tau;
+    const double denom = static_cast<double>(a.N) * static_cast<double>(no);
+    double v;
+    if (a.kind == 1) {
+        v = sum / denom;
+    } else if (tau == 0) {
+        v = 0.0;
+    } else {
+        const double P = a.S_prefix[no];
+        const double Q = a.S_prefix[a.T] - a.S_prefix[tau];
+        v = (P + Q - 2.0 * sum) / denom;
+    }
+    a.out[tau] = v;
 }
 
 __global__ void poly_reduce_kernel(const __grid_constant__ PolyReduceArgs a) {
-    const int64_t tau = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t tau = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (tau > a.tau_max) return;
-    poly_reduce_body(a, tau, threadIdx.x & 31);
+    poly_reduce_body(a, tau);
 }
 
 __global__ void poly_reduce_batch_kernel(const PolyReduceArgs *__restrict__ d, int n, int64_t total) {
-    const int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= total) return;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1081,7 +1188,7 @@ __global__ void poly_reduce_batch_kernel(const PolyReduceArgs *__restrict__ d, i
         if (d[mid].lag_begin <= g) lo = mid;
         else hi = mid - 1;
     }
-    poly_reduce_body(d[lo], g - d[lo].lag_begin, threadIdx.x & 31);
+    poly_reduce_body(d[lo], g - d[lo].lag_begin);
 }
 
 // ------------------------------------------------------------------ host
@@ -1158,7 +1265,7 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
     const size_t copies = size_t(8) * POLY_L * L->Kalloc * L->esize;
     L->off_xh = take(copies);
     L->off_xl = take(copies);
-    L->off_scale = take(size_t(POLY_L) * sizeof(float));
+    L->off_scale = take(size_t(2 * POLY_L) * sizeof(float));      // inv_scale, then row maxima
     L->off_S = take(kind == 0 ? size_t(T) * sizeof(double) : 0);
     L->off_prefix = take(kind == 0 ? size_t(T + 1) * sizeof(double) : 0);
     L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
@@ -1254,7 +1361,8 @@ cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, c
                                          static_cast<int>(SMEM_TOTAL));
     if (e != cudaSuccess) return e;
     prof_begin(kind, st);
-    gram_band_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(maps[0], maps[1], maps[2], maps[3], ga);
+    gram_band_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+                                                                      maps[5], ga);
     prof_end(st);
     return cudaGetLastError();
 }
@@ -1318,25 +1426,29 @@ int encode_maps(const GramLayout &L, uint8_t *base, int64_t s, CUtensorMap *maps
                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (A)");
-        CUresult rb;
-        if (s > 1) {
-            const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(s),
-                                        static_cast<cuuint64_t>(L.n_k)};
-            const cuuint64_t strB[2] = {rowb, rowb * static_cast<cuuint64_t>(s)};
-            const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), 1, static_cast<cuuint32_t>(BF)};
-            const cuuint32_t es3[3] = {1, 1, 1};
-            rb = encode(&maps[2 + h], dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        } else {
-            const cuuint64_t dimB[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.n_k)};
-            const cuuint64_t strB[1] = {rowb};
-            const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BF)};
-            rb = encode(&maps[2 + h], dt, 2, bases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        for (int v = 0; v < 2; ++v) {          // B with BF-row boxes, then with NBOX-row boxes
+            const cuuint32_t rows = static_cast<cuuint32_t>(v == 0 ? BF : NBOX);
+            CUtensorMap *mB = &maps[2 + 2 * v + h];
+            CUresult rb;
+            if (s > 1) {
+                const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(s),
+                                            static_cast<cuuint64_t>(L.n_k)};
+                const cuuint64_t strB[2] = {rowb, rowb * static_cast<cuuint64_t>(s)};
+                const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), 1, rows};
+                const cuuint32_t es3[3] = {1, 1, 1};
+                rb = encode(mB, dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            } else {
+                const cuuint64_t dimB[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.n_k)};
+                const cuuint64_t strB[1] = {rowb};
+                const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(L.bke), rows};
+                rb = encode(mB, dt, 2, bases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
+            if (rb != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (B)");
         }
-        if (rb != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (B)");
     }
     return TCORR_OK;
 }
@@ -1378,7 +1490,7 @@ struct BatchLayout {
     std::vector<GramLayout> L;
     std::vector<size_t> base;
     size_t off_inst = 0, off_split = 0, off_pfx = 0, off_red = 0, off_counter = 0, total = 0;
-    size_t off_pprep = 0, off_pred = 0;
+    size_t off_pprep = 0, off_pred = 0, off_rowmax = 0;
     int64_t total_items = 0, total_frames = 0, total_pfx = 0, total_lags = 0;
 };
 
@@ -1410,11 +1522,12 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     B->off_counter = take(sizeof(unsigned long long));
     B->off_pprep = take(sizeof(PolyPrepArgs) * count);
     B->off_pred = take(sizeof(PolyReduceArgs) * count);
+    B->off_rowmax = take(sizeof(unsigned) * POLY_L * count);    // polyphase row maxima, one reset
     B->base.resize(count);
     for (int k = 0; k < count; ++k) {
         const int i = B->order[k];
         B->base[i] = take(B->L[i].total);
-        if (B->L[i].poly) continue;      // polyphase instances run on their own
+        if (B->L[i].poly) continue;      // polyphase instances have prep and reduction of their own
         B->total_items += B->L[i].p.n_items;
         B->total_frames += B->L[i].T_pad;
         if (items[i].kind == 0) B->total_pfx += B->L[i].p.n_res;
@@ -1445,7 +1558,10 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     pa.Yh = base + L.off_xh;
     pa.Yl = base + L.off_xl;
     pa.inv_scale = reinterpret_cast<float *>(base + L.off_scale);
+    pa.rowmax = reinterpret_cast<unsigned *>(base + L.off_scale) + POLY_L;
     pa.kind = kind;
+    pa.rm_begin = 0;
+    pa.tile_begin = 0;
     EncodeFn encode = get_encode();
     if (!encode) return TCORR_EUNSUPPORTED;
     const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -1465,12 +1581,15 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase A)");
         const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kalloc), POLY_L, 8};
         const cuuint64_t strB[2] = {rowb, rowb * POLY_L};
-        const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BF), 1};
         const cuuint32_t es3[3] = {1, 1, 1};
-        if (encode(&maps[2 + h], dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase B)");
+        for (int v = 0; v < 2; ++v) {          // B with BF-row boxes, then with NBOX-row boxes
+            const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(v == 0 ? BF : NBOX),
+                                        1};
+            if (encode(&maps[2 + 2 * v + h], dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase B)");
+        }
     }
     GramArgs &ga = P->gram.ga;
     ga = GramArgs{};
@@ -1506,6 +1625,26 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     return TCORR_OK;
 }
 
+// Operand copies of one instance (single: *args by value) or of a batch
+// (batch: args points at n device descriptors), `grid` prep tiles.
+cudaError_t poly_split_launch(int prec, bool batch, const PolyPrepArgs *args, int n, unsigned grid,
+                              cudaStream_t st) {
+    auto go = [&](auto single_k, auto batch_k) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(batch ? reinterpret_cast<const void *>(batch_k)
+                                                   : reinterpret_cast<const void *>(single_k),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(PT_SMEM));
+        if (e != cudaSuccess) return e;
+        if (batch) batch_k<<<grid, PREP_THREADS, PT_SMEM, st>>>(args, n);
+        else single_k<<<grid, PREP_THREADS, PT_SMEM, st>>>(*args);
+        return cudaGetLastError();
+    };
+    switch (prec) {
+        case P_FP16: return go(poly_split_kernel<P_FP16>, poly_split_batch_kernel<P_FP16>);
+        case P_BF16: return go(poly_split_kernel<P_BF16>, poly_split_batch_kernel<P_BF16>);
+        default: return go(poly_split_kernel<P_TF32>, poly_split_batch_kernel<P_TF32>);
+    }
+}
+
 // S(t) and its prefix sums for a polyphase MSD instance.
 cudaError_t poly_msd_s(const float *d_x, const GramLayout &L, uint8_t *base, cudaStream_t st) {
     const int64_t T = L.p.T;
@@ -1523,14 +1662,16 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
     PolySetup P;
     int rc = poly_setup(kind, d_x, L, base, d_out, &P);
     if (rc != TCORR_OK) return rc;
-    const unsigned g = 8 * POLY_L;
-    switch (L.prec) {
-        case P_FP16: poly_split_kernel<P_FP16><<<g, PREP_THREADS, 0, st>>>(P.prep); break;
-        case P_BF16: poly_split_kernel<P_BF16><<<g, PREP_THREADS, 0, st>>>(P.prep); break;
-        default: poly_split_kernel<P_TF32><<<g, PREP_THREADS, 0, st>>>(P.prep); break;
+    cudaError_t e = cudaSuccess;
+    if (L.prec == P_FP16) {
+        if ((e = cudaMemsetAsync(P.prep.rowmax, 0, POLY_L * sizeof(unsigned), st)) != cudaSuccess)
+            return cuda_fail(e, "row-max reset");
+        poly_rowmax_kernel<<<static_cast<unsigned>(poly_rm_blocks(L.P)), POLY_L, 0, st>>>(P.prep);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_rowmax_kernel launch");
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "poly_split_kernel launch");
+    if ((e = poly_split_launch(L.prec, false, &P.prep, 1, static_cast<unsigned>(poly_tiles(L.Kalloc)), st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "poly_split_kernel launch");
     if (kind == 0 && (e = poly_msd_s(d_x, L, base, st)) != cudaSuccess) return cuda_fail(e, "poly S launch");
     const GramArgs &ga = P.gram.ga;
     if ((e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
@@ -1543,7 +1684,7 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
         default: e = launch_gram<P_TF32, false>(P.gram.maps, ga, grid, st, kind); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel (polyphase) launch");
-    poly_reduce_kernel<<<static_cast<unsigned>(ceil_div((L.p.tau_max + 1) * 32, 256)), 256, 0, st>>>(P.red);
+    poly_reduce_kernel<<<static_cast<unsigned>(ceil_div(L.p.tau_max + 1, 256)), 256, 0, st>>>(P.red);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_reduce launch");
     return TCORR_OK;
 }
@@ -1606,7 +1747,7 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "s_prefix_kernel launch");
     }
-    CUtensorMap maps[4];
+    CUtensorMap maps[NMAPS];
     const int rc = encode_maps(L, ws, s, maps);
     if (rc != TCORR_OK) return rc;
     const GramArgs ga = gram_args(L, ws, T, N, tau_max, s);
@@ -1714,7 +1855,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     std::vector<PolyPrepArgs> pprep;
     std::vector<PolyReduceArgs> pred;
     std::vector<int> poly_msd;
-    int64_t plag_begin = 0;
+    int64_t plag_begin = 0, prm_begin = 0, ptile_begin = 0;
     int nb = 0;                          // band instances, in descriptor order
     for (int k = 0; k < count; ++k) {
         const int i = B.order[k];
@@ -1732,6 +1873,11 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
                 item_begin += L.p.n_items;
                 inst.push_back(P.gram);
             }
+            P.prep.rowmax = reinterpret_cast<unsigned *>(ws + B.off_rowmax) + pprep.size() * POLY_L;
+            P.prep.rm_begin = prm_begin;
+            P.prep.tile_begin = ptile_begin;
+            prm_begin += poly_rm_blocks(L.P);
+            ptile_begin += poly_tiles(L.Kalloc);
             pprep.push_back(P.prep);
             P.red.lag_begin = plag_begin;
             plag_begin += it.tau_max + 1;
@@ -1780,13 +1926,14 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         return cuda_fail(e, "descriptor upload");
     if (np > 0) {
         const PolyPrepArgs *d_pp = reinterpret_cast<const PolyPrepArgs *>(ws + B.off_pprep);
-        const unsigned gp = static_cast<unsigned>(np) * 8u * POLY_L;
-        switch (B.prec) {
-            case P_FP16: poly_split_batch_kernel<P_FP16><<<gp, PREP_THREADS, 0, st>>>(d_pp, np); break;
-            case P_BF16: poly_split_batch_kernel<P_BF16><<<gp, PREP_THREADS, 0, st>>>(d_pp, np); break;
-            default: poly_split_batch_kernel<P_TF32><<<gp, PREP_THREADS, 0, st>>>(d_pp, np); break;
+        if (B.prec == P_FP16) {
+            if ((e = cudaMemsetAsync(ws + B.off_rowmax, 0, sizeof(unsigned) * POLY_L * np, st)) != cudaSuccess)
+                return cuda_fail(e, "row-max reset");
+            poly_rowmax_batch_kernel<<<static_cast<unsigned>(prm_begin), POLY_L, 0, st>>>(d_pp, np);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_rowmax_batch_kernel launch");
         }
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_split_batch_kernel launch");
+        if ((e = poly_split_launch(B.prec, true, d_pp, np, static_cast<unsigned>(ptile_begin), st)) != cudaSuccess)
+            return cuda_fail(e, "poly_split_batch_kernel launch");
         for (int i : poly_msd)
             if ((e = poly_msd_s(items[i].d_x, B.L[i], ws + B.base[i], st)) != cudaSuccess)
                 return cuda_fail(e, "poly S launch");
@@ -1839,7 +1986,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         if (e != cudaSuccess) return cuda_fail(e, "lag_reduce_batch launch");
     }
     if (np > 0) {
-        poly_reduce_batch_kernel<<<static_cast<unsigned>(ceil_div(plag_begin * 32, 256)), 256, 0, st>>>(
+        poly_reduce_batch_kernel<<<static_cast<unsigned>(ceil_div(plag_begin, 256)), 256, 0, st>>>(
             reinterpret_cast<const PolyReduceArgs *>(ws + B.off_pred), np, plag_begin);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_reduce_batch launch");
     }
