@@ -165,6 +165,46 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
                 size_t ws_bytes, void *stream);
 
 /*
+ * Streamed (out-of-core) MSD / autocorrelation of a trajectory held in HOST
+ * memory, for trajectories larger than device memory.  The paper's method
+ * needs every frame on the device (its Conclusion names this as the limit for
+ * dynamic quantities and leaves splitting a trajectory to the user); this
+ * entry point removes that limit.  Result: Eq. 5 (tcorr_msd_stream) or the
+ * autocorrelation of Eq. 4 (tcorr_acf_stream), exactly as tcorr_msd /
+ * tcorr_acf define it over the whole trajectory, up to rounding order.
+ * Method: the origins are cut into windows of chunk_frames frames (rounded up
+ * to a multiple of stride; 0 picks max(4 (tau_max + 1), 4096) rounded up to
+ * 128 stride).  Window c holds frames [c C, c C + C + tau_max); its first C
+ * frames are the origins it owns, the rest is the tau_max halo of partner
+ * frames.  Each window runs the tensor-core band kernel (or the plain
+ * kernel) restricted to its own origins and adds the per-lag numerators into
+ * d_out; one last kernel divides by N n_o(tau) of the whole trajectory.  Two
+ * window buffers alternate: the halo is copied from the previous window on
+ * the device and only the C new frames come from the host, on a second
+ * stream that overlaps the previous window's kernels.  Polyphase (small K)
+ * is not used in this mode; the band form handles every K.
+ * h_x   : [T][N][3] float32 in host memory, 4-byte aligned.  Pinned memory
+ *         (cudaHostAlloc / cudaHostRegister) lets the copies overlap the
+ *         kernels; pageable memory works but each copy then blocks the host.
+ *         h_x must stay valid and unchanged until `stream` has finished.
+ * d_out : tau_max+1 doubles on the device, 8-byte aligned (overwritten).
+ * d_ws  : device workspace of ws_bytes >= tcorr_stream_workspace_size(...),
+ *         256-byte aligned: two window buffers of min(T, C + tau_max) frames
+ *         plus the engine's workspace for one window.
+ * The call enqueues work on `stream` and on a stream of its own, joined back
+ * to `stream` through events; it cannot be captured in a CUDA graph.
+ * Errors: as tcorr_msd, plus TCORR_EINVAL for chunk_frames < 0.
+ */
+size_t tcorr_stream_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                                   int method, int64_t chunk_frames);
+int tcorr_msd_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                     int method, int64_t chunk_frames, double *d_out, void *d_ws,
+                     size_t ws_bytes, void *stream);
+int tcorr_acf_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                     int method, int64_t chunk_frames, double *d_out, void *d_ws,
+                     size_t ws_bytes, void *stream);
+
+/*
  * Plain FP32 path without a caller workspace: the same result, bit for bit,
  * as tcorr_msd (kind 0) or tcorr_acf (kind 1) with method TCORR_PLAIN, but
  * the library allocates nothing and the caller passes no workspace.  The

@@ -21,12 +21,14 @@ int plain_tile_bf();
 int plain_tile_wp();
 
 // Tensor-core path (gram_tc.cu).
-size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method);
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+                           const Window *w = nullptr);
 size_t gram_batch_workspace_size(const tcorr_instance *items, int count, int method);
 int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_ws, size_t ws_bytes,
                    cudaStream_t st);
 int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
-             int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st);
+             int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st,
+             const Window *w = nullptr);
 bool gram_method_available(int method);
 int status_poll_and_clear(cudaStream_t st);
 int selftest_timeout(cudaStream_t st);
@@ -59,6 +61,13 @@ BandPlan make_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int BO
     return p;
 }
 
+void cap_origins(BandPlan *p, int64_t cap) {
+    if (cap <= 0 || cap >= p->n_orig) return;
+    p->n_orig = cap;
+    p->n_rows = ceil_div(cap, p->BO);
+    p->n_items = p->n_groups * p->n_res * p->n_rows * p->n_cols;
+}
+
 namespace {
 
 bool valid_sizes(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
@@ -86,6 +95,32 @@ int resolve_method(int method, int64_t T, int64_t N, int64_t tau_max, int64_t s)
     return gram_method_available(TCORR_TC_FP16X3) ? TCORR_TC_FP16X3 : TCORR_PLAIN;
 }
 
+}  // namespace
+
+// Plain FP32 path for one trajectory, or one window of it (w != nullptr).
+int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
+              void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w) {
+    BandPlan p = make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg, kMinItems);
+    if (w) cap_origins(&p, w->orig_cap);
+    const size_t need = align256(sizeof(double) * static_cast<size_t>(p.n_items) * p.WP);
+    if (ws_bytes < need || (need > 0 && !d_ws)) return TCORR_EWORKSPACE;
+    double *partial = static_cast<double *>(d_ws);
+    cudaError_t e = launch_plain_tiles(kind, d_x, p, partial, st);
+    if (e != cudaSuccess) return cuda_fail(e, "plain_tile_kernel launch");
+    FinalizeArgs fa{0, nullptr, 0};
+    e = launch_lag_reduce(p, partial, fa, d_out, st, w);
+    if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
+    return TCORR_OK;
+}
+
+size_t plain_window_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s, int64_t orig_cap) {
+    BandPlan p = make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg, kMinItems);
+    cap_origins(&p, orig_cap);
+    return align256(sizeof(double) * static_cast<size_t>(p.n_items) * p.WP);
+}
+
+namespace {
+
 int run_corr(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
              int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
     if (!d_x || !d_out) return TCORR_EINVAL;
@@ -97,18 +132,7 @@ int run_corr(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (m != TCORR_PLAIN)
         return gram_run(kind, d_x, T, N, tau_max, s, m, d_out, d_ws, ws_bytes, st);
-
-    const BandPlan p = make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg,
-                                      kMinItems);
-    const size_t need = align256(sizeof(double) * static_cast<size_t>(p.n_items) * p.WP);
-    if (ws_bytes < need || (need > 0 && !d_ws)) return TCORR_EWORKSPACE;
-    double *partial = static_cast<double *>(d_ws);
-    cudaError_t e = launch_plain_tiles(kind, d_x, p, partial, st);
-    if (e != cudaSuccess) return cuda_fail(e, "plain_tile_kernel launch");
-    FinalizeArgs fa{0, nullptr, 0};
-    e = launch_lag_reduce(p, partial, fa, d_out, st);
-    if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
-    return TCORR_OK;
+    return plain_run(kind, d_x, T, N, tau_max, s, d_out, d_ws, ws_bytes, st, nullptr);
 }
 
 // ------------------------------------------------------------------ batch

@@ -1274,12 +1274,15 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
     return true;
 }
 
-bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int kind, GramLayout *L) {
+// w != nullptr: one window of a streamed trajectory (band form only: the
+// polyphase contraction cannot stop origins at a cap).
+bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int kind, GramLayout *L,
+                 const Window *w = nullptr) {
     if (!method_prec(method, &L->prec, &L->x4)) return false;
     L->esize = L->prec == P_TF32 ? 4 : 2;
     L->bke = L->prec == P_TF32 ? 16 : 32;
     const int64_t K = 3 * N;
-    L->poly = use_polyphase(T, N, tau_max, s);
+    L->poly = !w && use_polyphase(T, N, tau_max, s);
     if (L->poly) return make_poly_layout(T, N, tau_max, method, kind, L);
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
@@ -1298,6 +1301,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
         L->sub_kb = c.sub_kb;
     }
     L->p = make_band_plan(T, N, tau_max, s, BO, BF, L->kseg, 1);
+    if (w) cap_origins(&L->p, w->orig_cap);
     L->p.WP = WPG;
     // one K group per segment of kseg elements
     const int64_t kb_total = ceil_div(K, L->bke);
@@ -1693,11 +1697,11 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
 
 // Workspace bound: the MSD layout (a superset of the ACF one) with the chosen
 // parameters, and with the shortest candidate work item when tuning may run.
-size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method) {
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, const Window *w) {
     GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, 0, &L)) return 0;
+    if (!make_layout(T, N, tau_max, s, method, 0, &L, w)) return 0;
     size_t need = L.total;
-    if (tune_mode() != 0) {
+    if (!w && tune_mode() != 0) {
         const TuneChoice shortest{tune_min_kseg(), kSubKb};
         const TuneChoice *prev = get_tune_override();
         set_tune_override(&shortest);
@@ -1724,9 +1728,9 @@ bool gram_method_available(int method) {
 namespace {
 
 int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-                  double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+                  double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w = nullptr) {
     GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, kind, &L)) return TCORR_EUNSUPPORTED;
+    if (!make_layout(T, N, tau_max, s, method, kind, &L, w)) return TCORR_EUNSUPPORTED;
     if (ws_bytes < L.total || !d_ws) return TCORR_EWORKSPACE;
     int num_sms = 0;
     if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
@@ -1761,7 +1765,7 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
         default: e = launch_gram<P_TF32, false>(maps, ga, grid, st, kind); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
-    e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st);
+    e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st, w);
     if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
     return TCORR_OK;
 }
@@ -1807,7 +1811,8 @@ int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int
 }  // namespace
 
 int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st) {
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w) {
+    if (w) return gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, w);
     const int mode = tune_mode();
     if (mode != 0 && !env_kseg() && !env_sub_kb()) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

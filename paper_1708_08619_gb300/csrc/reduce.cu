@@ -40,8 +40,9 @@ __device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t 
     }
     const double D = warp_sum(sum);
     if (lane == 0) {
-        const int64_t no = n_origins(a.T, a.s, tau);
-        const double denom = static_cast<double>(a.N) * static_cast<double>(no);
+        int64_t no = n_origins(a.T, a.s, tau);
+        if (no > a.n_orig) no = a.n_orig;
+        const double denom = a.accumulate ? 1.0 : static_cast<double>(a.N) * static_cast<double>(no);
         double v;
         if (a.mode == 0) {
             v = D / denom;
@@ -57,7 +58,8 @@ __device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t 
             const double Q = pr[qq + no] - pr[qq];
             v = (P + Q - 2.0 * D) / denom;
         }
-        a.out[tau] = v;
+        if (a.accumulate) a.out[tau] += v;
+        else a.out[tau] = v;
     }
 }
 
@@ -194,16 +196,36 @@ LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const Fi
     a.prefix_stride = fa.prefix_stride;
     a.out = d_out;
     a.lag_begin = lag_begin;
+    a.n_orig = p.n_orig;
+    a.accumulate = 0;
     return a;
 }
 
 cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
-                              double *d_out, cudaStream_t st) {
-    const LagReduceDesc a = lag_reduce_desc(p, partial, fa, d_out, 0);
+                              double *d_out, cudaStream_t st, const Window *w) {
+    LagReduceDesc a = lag_reduce_desc(p, partial, fa, d_out, 0);
+    if (w && w->accumulate) a.accumulate = 1;
     const int64_t warps = p.tau_max + 1;
     const int threads = 256;
     const int64_t blocks = ceil_div(warps * 32, threads);
     lag_reduce_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void normalize_kernel(double *out, int64_t T, int64_t N, int64_t tau_max, int64_t s, int kind) {
+    const int64_t tau = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (tau > tau_max) return;
+    if (kind == 0 && tau == 0) {
+        out[0] = 0.0;
+        return;
+    }
+    out[tau] /= static_cast<double>(N) * static_cast<double>(n_origins(T, s, tau));
+}
+
+cudaError_t launch_normalize(double *d_out, int64_t T, int64_t N, int64_t tau_max, int64_t s, int kind,
+                             cudaStream_t st) {
+    normalize_kernel<<<static_cast<unsigned>(ceil_div(tau_max + 1, 256)), 256, 0, st>>>(d_out, T, N, tau_max, s,
+                                                                                         kind);
     return cudaGetLastError();
 }
 

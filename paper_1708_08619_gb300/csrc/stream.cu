@@ -1,0 +1,188 @@
+// Streamed (out-of-core) correlation of a trajectory held in host memory.
+//
+// The whole-trajectory path needs X[T][N][3] resident on the device; the
+// paper's Conclusion names that as the limit for dynamic quantities such as
+// the MSD (all frames of a species on the device), and its two-particle
+// section leaves splitting a trajectory to the user.  Here
+// the origins are cut into windows of C frames: window c holds frames
+// [cC, min(T, cC + C + tau_max)), i.e. its C origins plus a tau_max halo of
+// partner frames.  Every pair (t0, t0 + tau) with t0 in the window's first C
+// frames lies inside the window, so the windows together see each pair of
+// Eq. 5 (MSD) and of the ACF numerator (Eq. 4) exactly once.  Each window
+// runs the same engine as the whole-trajectory call, with its origins capped
+// at C and its per-lag numerators added into d_out; one last kernel divides
+// by N n_o(tau) of the whole trajectory.
+//
+// Copies: two window buffers alternate.  Window c's halo (its first tau_max
+// frames) is the tail of window c-1 and is copied device to device; only the
+// C new frames cross from the host, so each frame crosses once.  Copies run
+// on a second stream and overlap the previous window's kernels; events order
+// buffer reuse.
+#include <cstdint>
+
+#include "tcorr_internal.cuh"
+
+namespace tcorr {
+
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, const Window *w);
+int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w);
+bool gram_method_available(int method);
+int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
+              void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w);
+size_t plain_window_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s, int64_t orig_cap);
+bool corr_sizes_valid(int64_t T, int64_t N, int64_t tau_max, int64_t s);
+
+namespace {
+
+// Origins per window when the caller passes 0: four halos' worth, at least
+// 4096 frames, whole 128-origin row tiles.
+int64_t default_chunk(int64_t tau_max, int64_t s) {
+    int64_t c = 4 * (tau_max + 1);
+    if (c < 4096) c = 4096;
+    const int64_t q = 128 * s;
+    return ceil_div(c, q) * q;
+}
+
+struct StreamPlan {
+    int method;                 // resolved (never TCORR_AUTO)
+    int64_t K, C, W, n_win;     // K = 3N; origins per window; largest window; windows
+    size_t off_buf[2], off_engine, engine_bytes, total;
+};
+
+int64_t window_frames(const StreamPlan &P, int64_t T, int64_t tau_max, int64_t c) {
+    const int64_t t0 = c * P.C, w = P.C + tau_max;
+    return T - t0 < w ? T - t0 : w;
+}
+
+Window window_of(const StreamPlan &P, int64_t Wc, int64_t s) {
+    const int64_t first = P.C < Wc ? P.C : Wc;          // frames whose origins start pairs here
+    return Window{(first - 1) / s + 1, true};
+}
+
+bool make_stream_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int64_t chunk,
+                      StreamPlan *P) {
+    if (chunk < 0) return false;
+    P->method = method;
+    if (method == TCORR_AUTO) P->method = gram_method_available(TCORR_TC_FP16X3) ? TCORR_TC_FP16X3 : TCORR_PLAIN;
+    P->K = 3 * N;
+    int64_t C = chunk > 0 ? chunk : default_chunk(tau_max, s);
+    C = ceil_div(C, s) * s;                              // windows start on origins
+    const int64_t Tcap = ceil_div(T, s) * s;
+    if (C > Tcap) C = Tcap;
+    P->C = C;
+    P->W = T < C + tau_max ? T : C + tau_max;
+    P->n_win = ceil_div(T, C);
+    const int64_t tm = tau_max < P->W - 1 ? tau_max : P->W - 1;
+    const Window w = window_of(*P, P->W, s);
+    P->engine_bytes = P->method == TCORR_PLAIN ? plain_window_workspace(P->W, N, tm, s, w.orig_cap)
+                                               : gram_workspace_size(P->W, N, tm, s, P->method, &w);
+    if (P->engine_bytes == 0 && P->method != TCORR_PLAIN) return false;
+    const size_t buf = align256(static_cast<size_t>(P->W) * static_cast<size_t>(P->K) * sizeof(float));
+    P->off_buf[0] = 0;
+    P->off_buf[1] = buf;
+    P->off_engine = 2 * buf;
+    P->total = 2 * buf + align256(P->engine_bytes);
+    return true;
+}
+
+// Owns the side stream and events of one call; destroying them with work
+// still queued is allowed (CUDA releases them when that work completes).
+struct StreamRes {
+    cudaStream_t side = nullptr;
+    cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    ~StreamRes() {
+        for (cudaEvent_t e : {start, copied[0], copied[1], freed[0], freed[1]})
+            if (e) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
+    }
+    cudaError_t init() {
+        cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        for (cudaEvent_t *p : {&start, &copied[0], &copied[1], &freed[0], &freed[1]})
+            if ((e = cudaEventCreateWithFlags(p, cudaEventDisableTiming)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+};
+
+int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+               int64_t chunk, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!h_x || !d_out) return TCORR_EINVAL;
+    if (!corr_sizes_valid(T, N, tau_max, s) || method < TCORR_PLAIN || method > TCORR_AUTO || chunk < 0)
+        return TCORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(h_x) & 3u) || (reinterpret_cast<uintptr_t>(d_out) & 7u) ||
+        (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+        return TCORR_EALIGN;
+    StreamPlan P;
+    if (!make_stream_plan(T, N, tau_max, s, method, chunk, &P)) return TCORR_EUNSUPPORTED;
+    if (ws_bytes < P.total || !d_ws) return TCORR_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    StreamRes R;
+    cudaError_t e = R.init();
+    if (e != cudaSuccess) return cuda_fail(e, "stream resources");
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    float *buf[2] = {reinterpret_cast<float *>(ws + P.off_buf[0]), reinterpret_cast<float *>(ws + P.off_buf[1])};
+    const size_t row = static_cast<size_t>(P.K) * sizeof(float);
+    if ((e = cudaMemsetAsync(d_out, 0, sizeof(double) * static_cast<size_t>(tau_max + 1), st)) != cudaSuccess)
+        return cuda_fail(e, "output reset");
+    // the copy stream starts after everything already queued on the caller's stream
+    if ((e = cudaEventRecord(R.start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(R.side, R.start, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream fork");
+    for (int64_t c = 0; c < P.n_win; ++c) {
+        const int b = static_cast<int>(c & 1);
+        const int64_t t0 = c * P.C, Wc = window_frames(P, T, tau_max, c);
+        if (c >= 2 && (e = cudaStreamWaitEvent(R.side, R.freed[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "buffer reuse wait");
+        int64_t have = 0;
+        if (c > 0) {        // halo: frames [t0, t0 + h) sit at frame C of the previous window
+            have = tau_max < Wc ? tau_max : Wc;
+            if (have > 0 &&
+                (e = cudaMemcpyAsync(buf[b], buf[1 - b] + static_cast<size_t>(P.C) * P.K, have * row,
+                                     cudaMemcpyDeviceToDevice, R.side)) != cudaSuccess)
+                return cuda_fail(e, "halo copy");
+        }
+        if (Wc > have &&
+            (e = cudaMemcpyAsync(buf[b] + static_cast<size_t>(have) * P.K, h_x + static_cast<size_t>(t0 + have) * P.K,
+                                 (Wc - have) * row, cudaMemcpyHostToDevice, R.side)) != cudaSuccess)
+            return cuda_fail(e, "window copy");
+        if ((e = cudaEventRecord(R.copied[b], R.side)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, R.copied[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "window copy event");
+        const int64_t tm = tau_max < Wc - 1 ? tau_max : Wc - 1;
+        const Window w = window_of(P, Wc, s);
+        const int rc = P.method == TCORR_PLAIN
+                           ? plain_run(kind, buf[b], Wc, N, tm, s, d_out, ws + P.off_engine, P.engine_bytes, st, &w)
+                           : gram_run(kind, buf[b], Wc, N, tm, s, P.method, d_out, ws + P.off_engine,
+                                      P.engine_bytes, st, &w);
+        if (rc != TCORR_OK) return rc;
+        if ((e = cudaEventRecord(R.freed[b], st)) != cudaSuccess) return cuda_fail(e, "window done event");
+    }
+    if ((e = launch_normalize(d_out, T, N, tau_max, s, kind, st)) != cudaSuccess)
+        return cuda_fail(e, "normalize launch");
+    return TCORR_OK;
+}
+
+}  // namespace
+}  // namespace tcorr
+
+using namespace tcorr;
+
+extern "C" size_t tcorr_stream_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                                              int method, int64_t chunk_frames) {
+    if (!corr_sizes_valid(T, N, tau_max, stride) || method < TCORR_PLAIN || method > TCORR_AUTO) return 0;
+    StreamPlan P;
+    if (!make_stream_plan(T, N, tau_max, stride, method, chunk_frames, &P)) return 0;
+    return P.total;
+}
+
+extern "C" int tcorr_msd_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                                int method, int64_t chunk_frames, double *d_out, void *d_ws, size_t ws_bytes,
+                                void *stream) {
+    return run_stream(0, h_x, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws, ws_bytes, stream);
+}
+
+extern "C" int tcorr_acf_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                                int method, int64_t chunk_frames, double *d_out, void *d_ws, size_t ws_bytes,
+                                void *stream) {
+    return run_stream(1, h_x, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws, ws_bytes, stream);
+}

@@ -62,6 +62,19 @@ __host__ __device__ inline int64_t n_frames_res(int64_t T, int64_t s, int64_t rh
 BandPlan make_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int BO, int BF,
                         int64_t kseg, int64_t min_items);
 
+// One time window of a longer trajectory (the streamed path): only the
+// window's first orig_cap origins (0: all) start pairs, and the lag
+// reduction adds the per-lag numerators, sum over origins of |x(t+tau) -
+// x(t)|^2 (MSD) or x(t).x(t+tau) (ACF), into the output instead of writing
+// averages.  Summed over windows that tile the origins, these are the
+// numerators of Eq. 5 and of the ACF (Eq. 4) over the whole trajectory.
+struct Window {
+    int64_t orig_cap;
+    bool accumulate;
+};
+// Restricts a plan to its first `cap` origins (row tiles and items shrink).
+void cap_origins(BandPlan *p, int64_t cap);
+
 // Maps a failed CUDA call to TCORR_ECUDA; with TCORR_VERBOSE set in the
 // environment it also prints the call site and CUDA's error string.
 inline int cuda_fail(cudaError_t e, const char *what) {
@@ -114,7 +127,11 @@ struct FinalizeArgs {
     int64_t prefix_stride;    // mode 1: entries per residue row of S_prefix
 };
 cudaError_t launch_lag_reduce(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
-                              double *d_out, cudaStream_t st);
+                              double *d_out, cudaStream_t st, const Window *w = nullptr);
+// out[tau] /= N n_o(tau) over the whole trajectory (MSD: out[0] = 0): turns
+// the numerators accumulated over windows into averages.
+cudaError_t launch_normalize(double *d_out, int64_t T, int64_t N, int64_t tau_max, int64_t s, int kind,
+                             cudaStream_t st);
 
 // One instance of the lag reduction (also one entry of a batch).
 struct LagReduceDesc {
@@ -126,6 +143,8 @@ struct LagReduceDesc {
     int64_t prefix_stride;
     double *out;
     int64_t lag_begin;        // batch: first global lag of this instance
+    int64_t n_orig;           // origins that start pairs (n_o(tau) is capped by it)
+    int accumulate;           // 1: out[tau] += numerator (streamed windows)
 };
 LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
                               double *d_out, int64_t lag_begin);

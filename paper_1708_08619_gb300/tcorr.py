@@ -57,6 +57,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tcorr_batch_workspace_size.restype = sz
     lib.tcorr_batch.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci, vp, sz, vp]
     lib.tcorr_batch.restype = ci
+    lib.tcorr_stream_workspace_size.argtypes = [i64, i64, i64, i64, ci, i64]
+    lib.tcorr_stream_workspace_size.restype = sz
+    for name in ("tcorr_msd_stream", "tcorr_acf_stream"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, i64, i64, i64, i64, ci, i64, vp, vp, sz, vp]
+        f.restype = ci
     lib.tcorr_plain_static.argtypes = [ci, vp, i64, i64, i64, i64, vp, vp]
     lib.tcorr_plain_static.restype = ci
     lib.tcorr_profile_enable.argtypes = [ci]
@@ -198,6 +204,47 @@ def tcorr_batch(instances, method=AUTO, ws=None, stream=None, device=None):
     rc = load().tcorr_batch(instances, len(instances), m, ws_ptr, ws_bytes, _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "tcorr_batch")
+
+
+def tcorr_stream_workspace_size(T: int, N: int, tau_max: int, stride: int = 1, method=AUTO,
+                                chunk_frames: int = 0) -> int:
+    return int(load().tcorr_stream_workspace_size(T, N, tau_max, stride, _method(method), chunk_frames))
+
+
+def _corr_stream(fname: str, x, tau_max: int, stride: int, method, chunk_frames: int, out, ws, stream, device):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.is_cuda:
+        raise TypeError("x must be a host (CPU) torch tensor; pin it for overlapped copies")
+    if x.dtype != torch.float32 or x.dim() != 3 or x.shape[2] != 3 or not x.is_contiguous():
+        raise TypeError("x must be a contiguous float32 tensor of shape [T][N][3]")
+    T, N, _ = x.shape
+    m = _method(method)
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = torch.empty(tau_max + 1, dtype=torch.float64, device=device)
+    need = tcorr_stream_workspace_size(T, N, tau_max, stride, m, chunk_frames)
+    if ws is None:
+        ws = _alloc_ws(need, device)
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = getattr(load(), fname)(x.data_ptr(), T, N, tau_max, stride, m, chunk_frames, out.data_ptr(),
+                                ws_ptr, ws_bytes, _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, fname)
+    return out
+
+
+def tcorr_msd_stream(x, tau_max: int, stride: int = 1, method=AUTO, chunk_frames: int = 0, out=None, ws=None,
+                     stream=None, device=None):
+    """MSD of a host-resident x[T][N][3] streamed through the device in windows
+    of chunk_frames origins (0: library default); result on the device."""
+    return _corr_stream("tcorr_msd_stream", x, tau_max, stride, method, chunk_frames, out, ws, stream, device)
+
+
+def tcorr_acf_stream(x, tau_max: int, stride: int = 1, method=AUTO, chunk_frames: int = 0, out=None, ws=None,
+                     stream=None, device=None):
+    """Autocorrelation of a host-resident A[T][N][3], streamed as tcorr_msd_stream."""
+    return _corr_stream("tcorr_acf_stream", x, tau_max, stride, method, chunk_frames, out, ws, stream, device)
 
 
 def tcorr_plain_static(kind: int, x, tau_max: int, stride: int = 1, out=None, stream=None):

@@ -125,3 +125,35 @@ def test_binding_refuses_cpu_tensors(lib):
     x = torch.zeros((10, 2, 3), dtype=torch.float32)
     with pytest.raises(TypeError):
         tcorr.tcorr_msd(x, 5)
+
+
+def call_msd_stream(lib, x=FAKE_X, T=100, N=10, tau_max=50, s=1, method=0, chunk=0, out=FAKE_OUT,
+                    ws=FAKE_WS, ws_bytes=0):
+    return lib.tcorr_msd_stream(x, T, N, tau_max, s, method, chunk, out, ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(x=None), dict(out=None), dict(T=0), dict(N=0), dict(tau_max=-1), dict(tau_max=100),
+    dict(s=0), dict(method=99), dict(chunk=-1),
+])
+def test_stream_invalid_arguments(lib, kw):
+    assert call_msd_stream(lib, **kw) == 1   # TCORR_EINVAL
+
+
+def test_stream_misaligned_and_workspace(lib):
+    assert call_msd_stream(lib, x=FAKE_X + 2) == 2
+    assert call_msd_stream(lib, out=FAKE_OUT + 4) == 2
+    assert call_msd_stream(lib, ws=FAKE_WS + 8) == 2
+    need = lib.tcorr_stream_workspace_size(100, 10, 50, 1, 0, 32)
+    assert need > 0
+    assert call_msd_stream(lib, chunk=32, ws_bytes=need - 1) == 4
+
+
+def test_stream_workspace_holds_two_windows(lib):
+    T, N, tm = 5000, 64, 300
+    small = lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 512)
+    big = lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 2048)
+    assert 2 * (512 + tm) * N * 3 * 4 <= small < big
+    # a chunk covering the whole trajectory is one window of T frames
+    assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 10 ** 9) >= 2 * T * N * 3 * 4
+    assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, -1) == 0
