@@ -151,6 +151,10 @@ def gpu_identifier(torch, dev):
 # from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
 # see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
 GRAM_WATER_TRAFFIC_BYTES = 8 * (1014.019e6 + 5.692e6)
+# Host-to-device bandwidth from pinned memory measured on the GB300 machine
+# (cudaMemcpyAsync on 1-8 streams and a kernel reading mapped host memory
+# all gave 211 GB/s): the floor of an end-to-end step that moves its inputs.
+H2D_GBS = 211.0
 
 
 def peaks():
@@ -312,16 +316,40 @@ def run_gpu(args, wl):
     vh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
     xh.copy_(x)
     vh.copy_(v)
-    x2 = torch.empty_like(x)
-    v2 = torch.empty_like(v)
     m_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
     c_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
-    copy_stream = torch.cuda.Stream(dev)
-    ev_x, ev_v = torch.cuda.Event(), torch.cuda.Event()
+    gk_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
+    D_host = torch.empty(2, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(1, min(args.steps, 5))
 
-    def e2e_step():
-        # both arrays go up on a copy stream; the MSD starts as soon as the positions are in
+    def timed_e2e(fn):
+        fn()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fn()
+        torch.cuda.synchronize()
+        return shard.max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+
+    def finish_on(st):
+        # GK + Einstein, then the results back to pinned host memory
+        tcorr.gk_integrate(out_c, wl["dt"], 1.0 / 3.0, out=out_gk, stream=st)
+        tcorr.einstein_slope(out_m, wl["dt"], 3, out=out_D, stream=st)
+        with torch.cuda.stream(st):
+            m_host.copy_(out_m, non_blocking=True)
+            c_host.copy_(out_c, non_blocking=True)
+            gk_host.copy_(out_gk, non_blocking=True)
+            D_host.copy_(out_D, non_blocking=True)
+        st.synchronize()
+
+    # (a) whole arrays up on a copy stream, then the in-core calls
+    x2 = torch.empty_like(x)
+    v2 = torch.empty_like(v)
+    copy_stream = torch.cuda.Stream(dev)
+    ev_x, ev_v = torch.cuda.Event(), torch.cuda.Event()
+
+    def e2e_incore():
         with torch.cuda.stream(copy_stream):
             x2.copy_(xh, non_blocking=True)
             ev_x.record(copy_stream)
@@ -331,22 +359,41 @@ def run_gpu(args, wl):
         tcorr.tcorr_msd(x2, tm, s, method, out=out_m, ws=ws, stream=stream)
         stream.wait_event(ev_v)
         tcorr.tcorr_acf(v2, tm, s, method, out=out_c, ws=ws, stream=stream)
-        with torch.cuda.stream(stream):
-            m_host.copy_(out_m, non_blocking=True)
-            c_host.copy_(out_c, non_blocking=True)
-        stream.synchronize()
+        finish_on(stream)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = u_step * world / shard.max_over_ranks(e2e_s)
+    e2e_incore_s = timed_e2e(e2e_incore)
+    del x2, v2
+
+    # (b) the streamed calls, MSD and VACF on two streams with a workspace each:
+    # windows of C origins, host copies overlapping the kernels
+    C = args.stream_chunk
+    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ws_a = torch.empty(tcorr.tcorr_stream_workspace_size(T, N, tm, s, method, C), dtype=torch.uint8, device=dev)
+    ws_b = torch.empty(tcorr.tcorr_stream_workspace_size(T, N, tm, s, method, C), dtype=torch.uint8, device=dev)
+    ev_go = torch.cuda.Event()
+
+    def e2e_streamed():
+        ev_go.record(stream)
+        sa.wait_event(ev_go)
+        sb.wait_event(ev_go)
+        tcorr.tcorr_msd_stream(xh, tm, s, method, chunk_frames=C, out=out_m, ws=ws_a, stream=sa)
+        tcorr.tcorr_acf_stream(vh, tm, s, method, chunk_frames=C, out=out_c, ws=ws_b, stream=sb)
+        stream.wait_stream(sa)
+        stream.wait_stream(sb)
+        finish_on(stream)
+
+    e2e_stream_s = timed_e2e(e2e_streamed)
+    del ws_a, ws_b
+    e2e_s = min(e2e_stream_s, e2e_incore_s)
+    e2e_value = u_step * world / e2e_s
     h2d = 2 * T * N * 3 * 4
-    d2h = 2 * (tm + 1) * 8
+    d2h = (3 * (tm + 1) + 2) * 8
+    e2e_info = {"api": ("tcorr_msd_stream + tcorr_acf_stream on two streams, chunk_frames=%d" % C
+                        if e2e_stream_s <= e2e_incore_s else "host copies + tcorr_msd + tcorr_acf"),
+                "ms_per_step": e2e_s * 1e3,
+                "streamed_ms_per_step": e2e_stream_s * 1e3,
+                "incore_ms_per_step": e2e_incore_s * 1e3,
+                "h2d_link_bound_ms": h2d / H2D_GBS / 1e6}
 
     # ---- roofline of the dominant kernel (the MSD band kernel), timed alone
     pk, pk_kind = peaks()
@@ -419,8 +466,8 @@ def run_gpu(args, wl):
                        "msd_kernel_ms": msd_avg_s * 1000.0, "acf_kernel_ms": acf_avg_s * 1000.0,
                        "updates_per_step": u_step, "plain_comparison": plain_cmp},
             "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": dict({"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h}, **e2e_info),
             "gpu_launches": launches_per_step * args.steps,
             "roofline": roof,
             "cpu_baseline": cpu}
@@ -630,6 +677,8 @@ def main():
     ap.add_argument("--no-plain-compare", action="store_true")
     ap.add_argument("--workload", default="water", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stream-chunk", type=int, default=2048,
+                    help="origins per window of the streamed end-to-end calls")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
