@@ -151,10 +151,6 @@ def gpu_identifier(torch, dev):
 # from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
 # see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
 GRAM_WATER_TRAFFIC_BYTES = 8 * (1014.019e6 + 5.692e6)
-# Host-to-device bandwidth from pinned memory measured on the GB300 machine
-# (cudaMemcpyAsync on 1-8 streams and a kernel reading mapped host memory
-# all gave 211 GB/s): the floor of an end-to-end step that moves its inputs.
-H2D_GBS = 211.0
 
 
 def peaks():
@@ -384,6 +380,18 @@ def run_gpu(args, wl):
 
     e2e_stream_s = timed_e2e(e2e_streamed)
     del ws_a, ws_b
+    # this machine's host link: one pinned-to-device copy of 1 GiB, CUDA events
+    hb = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+    db = torch.empty(1 << 28, dtype=torch.float32, device=dev)
+    db.copy_(hb, non_blocking=True)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(3):
+        db.copy_(hb, non_blocking=True)
+    h1.record(stream)
+    h1.synchronize()
+    h2d_gbs = 3 * (1 << 30) / (h0.elapsed_time(h1) / 1e3) / 1e9
+    del hb, db
     e2e_s = min(e2e_stream_s, e2e_incore_s)
     e2e_value = u_step * world / e2e_s
     h2d = 2 * T * N * 3 * 4
@@ -393,7 +401,8 @@ def run_gpu(args, wl):
                 "ms_per_step": e2e_s * 1e3,
                 "streamed_ms_per_step": e2e_stream_s * 1e3,
                 "incore_ms_per_step": e2e_incore_s * 1e3,
-                "h2d_link_bound_ms": h2d / H2D_GBS / 1e6}
+                "h2d_gbs_measured": h2d_gbs,
+                "h2d_link_bound_ms": h2d / h2d_gbs / 1e6}
 
     # ---- roofline of the dominant kernel (the MSD band kernel), timed alone
     pk, pk_kind = peaks()

@@ -101,7 +101,8 @@ struct GramArgs {
     int64_t T, s, tau_max, n_orig, n_res, n_rows, n_cols, n_items;
     int64_t kb_total;       // K-blocks that hold data: ceil(K / BKe)
     int64_t kb_per_item;    // K-blocks per work item
-    const float *inv_scale; // per-frame 2^-e (FP16), or nullptr
+    const float *inv_scale; // 2^-e per frame (FP16): [group][scale_stride] (band) or [phase] (polyphase)
+    int64_t scale_stride;   // band: T_pad (one row of scales per K-group); polyphase: 0
     double *partial;        // [n_items][WPG]
     int b3d;                // B map is 3-D (K, residue, frame index) when s > 1
     int sub_kb;             // K-blocks per accumulation sub-chain
@@ -647,11 +648,12 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             float rs = 1.f;
             if (PREC == P_FP16) {
                 const int64_t nscale = a.mode == 0 ? a.T : 3 * BO;
+                const float *isc = a.inv_scale + (I.kb0 / a.kb_per_item) * a.scale_stride;
                 for (int j = et; j < BF; j += 32 * NEPI) {
                     const int64_t f = I.sb0 + j * I.sstr;
-                    cs[j] = f < nscale ? a.inv_scale[f] : 1.f;
+                    cs[j] = f < nscale ? isc[f] : 1.f;
                 }
-                rs = (row < I.a_rows) ? a.inv_scale[I.sa0 + row * I.sstr] : 1.f;
+                rs = (row < I.a_rows) ? isc[I.sa0 + row * I.sstr] : 1.f;
                 named_bar_sync(1, 32 * NEPI);
             }
             const int64_t mrow = I.moff - row;        // band offset / lag m = mrow + j
@@ -792,55 +794,134 @@ __device__ __forceinline__ void load8(const float *__restrict__ row, const float
     }
 }
 
+// One prep entry: an instance's frames cut into K-groups of kseg elements,
+// the K range one Gram work item contracts.  The FP16 scale and the FP64
+// partial of S(t) are kept per (group, frame): inv_scale[g][T_pad], S[g][T].
+struct SplitDesc {
+    const float *X;
+    int64_t T, K, Kp, T_pad, kseg, n_groups;
+    void *Xh, *Xl;
+    float *inv_scale;
+    double *S;
+    int kind, vec;
+    int64_t blk_begin;        // batch: first global block (frame x group) of this instance
+};
+
+// Block-wide max of |x| -> power-of-two scale 2^e with max |x| 2^e < 2^14,
+// so that FP16 hi and lo stay normal; stores 2^-e for the epilogue.
+__device__ __forceinline__ float fp16_scale(float mx, float *red_f, float *inv_out) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((tid & 31) == 0) red_f[tid >> 5] = mx;
+    __syncthreads();
+    mx = red_f[0];
+#pragma unroll
+    for (int i = 1; i < PREP_THREADS / 32; ++i) mx = fmaxf(mx, red_f[i]);
+    int e = 0;
+    if (mx > 0.f) {
+        int ex;
+        frexpf(mx, &ex);          // mx < 2^ex
+        e = 14 - ex;
+        e = e < -60 ? -60 : (e > 60 ? 60 : e);
+    }
+    if (tid == 0) *inv_out = ldexpf(1.f, -e);
+    return ldexpf(1.f, e);
+}
+
+// One block per (padded frame t, K-group g): x = r_t - r_0 (MSD) or A_t
+// (ACF) over the group's columns, scaled (FP16) and split into hi/lo, and the
+// group's part of S(t) = |x_t|^2 in FP64.  A group of up to 8 x 2048 columns
+// is held in registers: one read from DRAM, then the max, then the stores.
 template <int PREC, int KIND, bool VEC>
-__device__ __forceinline__ void split_body(const float *__restrict__ X, int64_t T, int64_t K, int64_t Kp,
-                                           void *Xh, void *Xl, float *inv_scale, double *S, int64_t t) {
+__device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_t g) {
     __shared__ float red_f[PREP_THREADS / 32];
     __shared__ double red_d[PREP_THREADS / 32];
     const int tid = threadIdx.x;
-    const bool live = t < T;
-    const float *row = X + (live ? t : 0) * K;
-    const int64_t Klive = live ? K : 0;      // padding rows are all zero
+    const float *X = q.X;
+    const bool live = t < q.T;
+    const float *row = X + (live ? t : 0) * q.K;
+    const int64_t Klive = live ? q.K : 0;      // padding rows are all zero
+    const int64_t kb = g * q.kseg;
+    const int64_t ke = g == q.n_groups - 1 ? q.Kp : min(q.Kp, kb + q.kseg);
     constexpr int64_t STEP = PREP_THREADS * 8;
+    constexpr int NCH = 8;
+    float *inv_out = q.inv_scale + g * q.T_pad + t;
     float scale = 1.f;
-    if (PREC == P_FP16) {
+    double sacc = 0.0;
+    if (ke - kb <= NCH * STEP) {
+        float x[NCH][8];
         float mx = 0.f;
-        for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < Klive; k0 += STEP) {
+        // MSD: the frame-0 values are loaded with their rows, half the chunks at a
+        // time, so that the loads in flight fit the registers
+        constexpr int NH = KIND == 0 ? NCH / 2 : NCH;
+#pragma unroll
+        for (int h = 0; h < NCH / NH; ++h) {
+            float r[KIND == 0 ? NH : 1][8];
+#pragma unroll
+            for (int cc = 0; cc < NH; ++cc) {
+                const int c = h * NH + cc;
+                const int64_t k0 = kb + c * STEP + static_cast<int64_t>(tid) * 8;
+                if (k0 < ke) {
+                    load8<1, VEC>(row, X, k0, Klive, x[c]);
+                    if (KIND == 0) load8<1, VEC>(X, X, k0, Klive, r[cc]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        x[c][i] = 0.f;
+                        if (KIND == 0) r[cc][i] = 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < NH; ++cc) {
+                const int c = h * NH + cc;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (KIND == 0) x[c][i] -= r[cc][i];
+                    mx = fmaxf(mx, fabsf(x[c][i]));
+                }
+            }
+        }
+        if (PREC == P_FP16) scale = fp16_scale(mx, red_f, inv_out);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int64_t k0 = kb + c * STEP + static_cast<int64_t>(tid) * 8;
+            if (k0 < ke) {
+                if (KIND == 0) {
+                    float sq = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) sq = fmaf(x[c][i], x[c][i], sq);
+                    sacc += static_cast<double>(sq);
+                }
+                split_store8<PREC>(x[c], scale, q.Xh, q.Xl, t * q.Kp + k0);
+            }
+        }
+    } else {
+        // a longer group: a max pass, then the conversion pass (second read from L2)
+        if (PREC == P_FP16) {
+            float mx = 0.f;
+            for (int64_t k0 = kb + static_cast<int64_t>(tid) * 8; k0 < ke; k0 += STEP) {
+                float x[8];
+                load8<KIND, VEC>(row, X, k0, Klive, x);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(x[i]));
+            }
+            scale = fp16_scale(mx, red_f, inv_out);
+        }
+        for (int64_t k0 = kb + static_cast<int64_t>(tid) * 8; k0 < ke; k0 += STEP) {
             float x[8];
             load8<KIND, VEC>(row, X, k0, Klive, x);
+            if (KIND == 0) {
+                float sq = 0.f;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(x[i]));
+                for (int i = 0; i < 8; ++i) sq = fmaf(x[i], x[i], sq);
+                sacc += static_cast<double>(sq);
+            }
+            split_store8<PREC>(x, scale, q.Xh, q.Xl, t * q.Kp + k0);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if ((tid & 31) == 0) red_f[tid >> 5] = mx;
-        __syncthreads();
-        mx = red_f[0];
-#pragma unroll
-        for (int i = 1; i < PREP_THREADS / 32; ++i) mx = fmaxf(mx, red_f[i]);
-        int e = 0;
-        if (mx > 0.f) {
-            int ex;
-            frexpf(mx, &ex);          // mx < 2^ex
-            e = 14 - ex;
-            e = e < -60 ? -60 : (e > 60 ? 60 : e);
-        }
-        scale = ldexpf(1.f, e);
-        if (tid == 0) inv_scale[t] = ldexpf(1.f, -e);
     }
-    double sacc = 0.0;
-    for (int64_t k0 = static_cast<int64_t>(tid) * 8; k0 < Kp; k0 += STEP) {
-        float x[8];
-        load8<KIND, VEC>(row, X, k0, Klive, x);
-        if (KIND == 0) {
-            float sq = 0.f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sq = fmaf(x[i], x[i], sq);
-            sacc += static_cast<double>(sq);
-        }
-        split_store8<PREC>(x, scale, Xh, Xl, t * Kp + k0);
-    }
-    if (KIND == 0 && S != nullptr) {
+    if (KIND == 0 && q.S != nullptr) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
         if ((tid & 31) == 0) red_d[tid >> 5] = sacc;
@@ -849,46 +930,34 @@ __device__ __forceinline__ void split_body(const float *__restrict__ X, int64_t 
             double tot = 0.0;
 #pragma unroll
             for (int i = 0; i < PREP_THREADS / 32; ++i) tot += red_d[i];
-            S[t] = tot;
+            q.S[g * q.T + t] = tot;
         }
     }
 }
 
 template <int PREC, int KIND, bool VEC>
-__global__ void __launch_bounds__(PREP_THREADS) split_kernel(const float *__restrict__ X, int64_t T,
-                                                             int64_t K, int64_t Kp, void *Xh, void *Xl,
-                                                             float *inv_scale, double *S) {
-    split_body<PREC, KIND, VEC>(X, T, K, Kp, Xh, Xl, inv_scale, S, blockIdx.x);
+__global__ void __launch_bounds__(PREP_THREADS, 2) split_kernel(const __grid_constant__ SplitDesc q) {
+    split_body<PREC, KIND, VEC>(q, blockIdx.x, blockIdx.y);
 }
 
-// One batch entry of the prep pass.
-struct SplitDesc {
-    const float *X;
-    int64_t T, K, Kp;
-    void *Xh, *Xl;
-    float *inv_scale;
-    double *S;
-    int kind, vec;
-    int64_t frame_begin;      // first global block (padded frame) of this instance
-};
-
 template <int PREC>
-__global__ void __launch_bounds__(PREP_THREADS) split_batch_kernel(const SplitDesc *__restrict__ d, int n) {
+__global__ void __launch_bounds__(PREP_THREADS, 2) split_batch_kernel(const SplitDesc *__restrict__ d, int n) {
     const int64_t b = blockIdx.x;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (d[mid].frame_begin <= b) lo = mid;
+        if (d[mid].blk_begin <= b) lo = mid;
         else hi = mid - 1;
     }
     const SplitDesc &q = d[lo];
-    const int64_t t = b - q.frame_begin;
+    const int64_t local = b - q.blk_begin;
+    const int64_t t = local / q.n_groups, g = local - t * q.n_groups;
     if (q.kind == 0) {
-        if (q.vec) split_body<PREC, 0, true>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
-        else split_body<PREC, 0, false>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
+        if (q.vec) split_body<PREC, 0, true>(q, t, g);
+        else split_body<PREC, 0, false>(q, t, g);
     } else {
-        if (q.vec) split_body<PREC, 1, true>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
-        else split_body<PREC, 1, false>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S, t);
+        if (q.vec) split_body<PREC, 1, true>(q, t, g);
+        else split_body<PREC, 1, false>(q, t, g);
     }
 }
 
@@ -921,8 +990,15 @@ __device__ __forceinline__ double block_exclusive_scan(double v, double *warp_to
     return warp_tot[w] + (inc - v);
 }
 
-__device__ __forceinline__ void s_prefix_body(const double *S, int64_t T, int64_t s, int64_t pstride,
-                                              double *prefix, int64_t rho) {
+// S(f) = sum over K-groups g of S[g][f], added in group order.
+__device__ __forceinline__ double s_total(const double *S, int64_t T, int64_t n_groups, int64_t f) {
+    double v = 0.0;
+    for (int64_t g = 0; g < n_groups; ++g) v += S[g * T + f];
+    return v;
+}
+
+__device__ __forceinline__ void s_prefix_body(const double *S, int64_t T, int64_t n_groups, int64_t s,
+                                              int64_t pstride, double *prefix, int64_t rho) {
     __shared__ double warp_tot[32];
     const int tid = threadIdx.x;
     const int64_t n = n_frames_res(T, s, rho);
@@ -930,23 +1006,31 @@ __device__ __forceinline__ void s_prefix_body(const double *S, int64_t T, int64_
     const int64_t per = ceil_div(n > 0 ? n : 1, PFX_THREADS);
     const int64_t b = tid * per, e = min(n, b + per);
     double acc = 0.0;
-    for (int64_t j = b; j < e; ++j) acc += S[rho + j * s];
+    for (int64_t j = b; j < e; ++j) acc += s_total(S, T, n_groups, rho + j * s);
     double run = block_exclusive_scan(acc, warp_tot);
     if (tid == 0) pr[0] = 0.0;
     for (int64_t j = b; j < e; ++j) {
-        run += S[rho + j * s];
+        run += s_total(S, T, n_groups, rho + j * s);
         pr[j + 1] = run;
     }
 }
 
-__global__ void __launch_bounds__(PFX_THREADS) s_prefix_kernel(const double *S, int64_t T, int64_t s,
-                                                                int64_t pstride, double *prefix) {
-    s_prefix_body(S, T, s, pstride, prefix, blockIdx.x);
+__global__ void __launch_bounds__(PFX_THREADS) s_prefix_kernel(const double *S, int64_t T, int64_t n_groups,
+                                                                int64_t s, int64_t pstride, double *prefix) {
+    s_prefix_body(S, T, n_groups, s, pstride, prefix, blockIdx.x);
+}
+
+// S[0][f] = sum over K-groups g of S[g][f] (group order), in place: then
+// the prefix pass reads one value per frame.
+__global__ void s_combine_kernel(double *S, int64_t T, int64_t n_groups) {
+    const int64_t f = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (f >= T) return;
+    S[f] = s_total(S, T, n_groups, f);
 }
 
 struct PfxDesc {
     const double *S;
-    int64_t T, s, pstride;
+    int64_t T, n_groups, s, pstride;
     double *prefix;
     int64_t blk_begin;        // first global block (residue) of this instance
 };
@@ -960,7 +1044,7 @@ __global__ void __launch_bounds__(PFX_THREADS) s_prefix_batch_kernel(const PfxDe
         else hi = mid - 1;
     }
     const PfxDesc &q = d[lo];
-    s_prefix_body(q.S, q.T, q.s, q.pstride, q.prefix, b - q.blk_begin);
+    s_prefix_body(q.S, q.T, q.n_groups, q.s, q.pstride, q.prefix, b - q.blk_begin);
 }
 
 // ------------------------------------------------------------- polyphase
@@ -1320,8 +1404,8 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     };
     L->off_xh = take(size_t(L->T_pad) * L->Kp * L->esize);
     L->off_xl = take(size_t(L->T_pad) * L->Kp * L->esize);
-    L->off_scale = take(size_t(L->T_pad) * sizeof(float));
-    L->off_S = take(kind == 0 ? size_t(T) * sizeof(double) : 0);
+    L->off_scale = take(size_t(L->p.n_groups) * L->T_pad * sizeof(float));
+    L->off_S = take(kind == 0 ? size_t(L->p.n_groups) * T * sizeof(double) : 0);
     L->off_prefix = take(kind == 0 ? size_t(L->p.n_res) * L->pstride * sizeof(double) : 0);
     L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
     L->off_counter = take(sizeof(unsigned long long));
@@ -1382,31 +1466,35 @@ cudaError_t launch_gram_batch(const SrcBatch &src, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *base, int64_t frame_begin) {
+SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *base, int64_t blk_begin) {
     SplitDesc q;
     q.X = X;
     q.T = L.p.T;
     q.K = L.p.K;
     q.Kp = L.Kp;
+    q.T_pad = L.T_pad;
+    q.kseg = (L.kseg / L.bke) * L.bke;     // the K range of one Gram work item
+    q.n_groups = L.p.n_groups;
     q.Xh = base + L.off_xh;
     q.Xl = base + L.off_xl;
     q.inv_scale = reinterpret_cast<float *>(base + L.off_scale);
     q.S = kind == 0 ? reinterpret_cast<double *>(base + L.off_S) : nullptr;
     q.kind = kind;
     q.vec = (q.K % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
-    q.frame_begin = frame_begin;
+    q.blk_begin = blk_begin;
     return q;
 }
 
 template <int PREC>
-cudaError_t launch_split(const SplitDesc &q, int64_t blocks, cudaStream_t st) {
-    const unsigned g = static_cast<unsigned>(blocks);
+cudaError_t launch_split(const SplitDesc &q, cudaStream_t st) {
+    if (q.n_groups > 65535 || q.T_pad > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const dim3 g(static_cast<unsigned>(q.T_pad), static_cast<unsigned>(q.n_groups));
     if (q.kind == 0) {
-        if (q.vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
-        else split_kernel<PREC, 0, false><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
+        if (q.vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(q);
+        else split_kernel<PREC, 0, false><<<g, PREP_THREADS, 0, st>>>(q);
     } else {
-        if (q.vec) split_kernel<PREC, 1, true><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
-        else split_kernel<PREC, 1, false><<<g, PREP_THREADS, 0, st>>>(q.X, q.T, q.K, q.Kp, q.Xh, q.Xl, q.inv_scale, q.S);
+        if (q.vec) split_kernel<PREC, 1, true><<<g, PREP_THREADS, 0, st>>>(q);
+        else split_kernel<PREC, 1, false><<<g, PREP_THREADS, 0, st>>>(q);
     }
     return cudaGetLastError();
 }
@@ -1472,6 +1560,7 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
     ga.kb_total = ceil_div(3 * N, L.bke);
     ga.kb_per_item = L.kseg / L.bke;
     ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
+    ga.scale_stride = L.T_pad;
     ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = s > 1 ? 1 : 0;
     ga.sub_kb = L.sub_kb;
@@ -1533,7 +1622,7 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
         B->base[i] = take(B->L[i].total);
         if (B->L[i].poly) continue;      // polyphase instances have prep and reduction of their own
         B->total_items += B->L[i].p.n_items;
-        B->total_frames += B->L[i].T_pad;
+        B->total_frames += B->L[i].T_pad * B->L[i].p.n_groups;     // prep blocks: frame x K-group
         if (items[i].kind == 0) B->total_pfx += B->L[i].p.n_res;
         B->total_lags += items[i].tau_max + 1;
     }
@@ -1655,7 +1744,7 @@ cudaError_t poly_msd_s(const float *d_x, const GramLayout &L, uint8_t *base, cud
     double *S = reinterpret_cast<double *>(base + L.off_S);
     double *prefix = reinterpret_cast<double *>(base + L.off_prefix);
     poly_s_kernel<<<static_cast<unsigned>(ceil_div(T, 256)), 256, 0, st>>>(d_x, T, 3 * L.p.N, S);
-    s_prefix_kernel<<<1, PFX_THREADS, 0, st>>>(S, T, 1, T + 1, prefix);
+    s_prefix_kernel<<<1, PFX_THREADS, 0, st>>>(S, T, 1, 1, T + 1, prefix);
     return cudaGetLastError();
 }
 
@@ -1740,14 +1829,17 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     const SplitDesc q = split_desc(kind, d_x, L, ws, 0);
     cudaError_t e;
     switch (L.prec) {
-        case P_FP16: e = launch_split<P_FP16>(q, L.T_pad, st); break;
-        case P_BF16: e = launch_split<P_BF16>(q, L.T_pad, st); break;
-        default: e = launch_split<P_TF32>(q, L.T_pad, st); break;
+        case P_FP16: e = launch_split<P_FP16>(q, st); break;
+        case P_BF16: e = launch_split<P_BF16>(q, st); break;
+        default: e = launch_split<P_TF32>(q, st); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "split_kernel launch");
     if (kind == 0) {
+        double *S = reinterpret_cast<double *>(ws + L.off_S);
+        if (L.p.n_groups > 1)
+            s_combine_kernel<<<static_cast<unsigned>(ceil_div(T, 256)), 256, 0, st>>>(S, T, L.p.n_groups);
         s_prefix_kernel<<<static_cast<unsigned>(L.p.n_res), PFX_THREADS, 0, st>>>(
-            reinterpret_cast<double *>(ws + L.off_S), T, s, L.pstride, reinterpret_cast<double *>(ws + L.off_prefix));
+            S, T, 1, s, L.pstride, reinterpret_cast<double *>(ws + L.off_prefix));
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "s_prefix_kernel launch");
     }
@@ -1903,11 +1995,12 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             inst.push_back(d);
         }
         spl[nb] = split_desc(it.kind, it.d_x, L, base, frame_begin);
-        frame_begin += L.T_pad;
+        frame_begin += L.T_pad * L.p.n_groups;
         if (it.kind == 0) {
             PfxDesc q;
             q.S = reinterpret_cast<const double *>(base + L.off_S);
             q.T = it.T;
+            q.n_groups = L.p.n_groups;
             q.s = it.stride;
             q.pstride = L.pstride;
             q.prefix = reinterpret_cast<double *>(base + L.off_prefix);

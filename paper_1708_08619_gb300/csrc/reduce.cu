@@ -91,45 +91,71 @@ __global__ void write_bytes_kernel(uint8_t *dst, const __grid_constant__ ByteChu
     for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.bytes[i];
 }
 
-// Running trapezoid.  One block: thread t owns a contiguous chunk of the
-// increments dt (c[k-1] + c[k]) / 2, the chunk totals are combined by a fixed
-// warp-shuffle scan, then each thread writes its running values.
-constexpr int GK_THREADS = 1024;
+// Running trapezoid, I(k) = I(k-1) + dt (c[k-1] + c[k]) / 2, spread over
+// blocks of GK_SPAN increments (FP64 throughput per SM is low on this part,
+// so one block would be slow).  Block b first sums the values before its
+// span, sum_{k<k0} c[k], strided over its threads in a fixed order, which
+// gives the integral up to its start as dt (2 S - c[0] - c[k0-1]) / 2; then
+// each thread integrates GK_PER increments and a fixed warp-shuffle scan
+// combines them.  Deterministic for a given n.
+constexpr int GK_THREADS = 256;
+constexpr int GK_PER = 8;
+constexpr int64_t GK_SPAN = int64_t(GK_THREADS) * GK_PER;
+
+__device__ __forceinline__ double block_allsum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < GK_THREADS / 32; ++i) r += sh[i];
+    __syncthreads();
+    return r;
+}
 
 __global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *c, int64_t n, double dt,
                                                                    double prefactor, double *running) {
-    __shared__ double warp_tot[32];
+    __shared__ double sh[GK_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int64_t nseg = n - 1;                     // increments k = 1 .. n-1
-    const int64_t per = ceil_div(nseg > 0 ? nseg : 1, GK_THREADS);
-    const int64_t b = 1 + t * per;
-    const int64_t e = min(n, b + per);
-    double acc = 0.0;
-    for (int64_t k = b; k < e; ++k) acc += dt * (c[k - 1] + c[k]) / 2.0;
-    double inc = acc;
+    const int64_t k0 = 1 + static_cast<int64_t>(blockIdx.x) * GK_SPAN;    // first increment of the span
+    double before = 0.0;
+    if (k0 > 1) {
+        double S = 0.0;
+        for (int64_t k = t; k < k0; k += GK_THREADS) S += c[k];
+        S = block_allsum(S, sh);
+        before = dt * (2.0 * S - c[0] - c[k0 - 1]) / 2.0;
+    }
+    const int64_t kb = k0 + static_cast<int64_t>(t) * GK_PER;
+    double loc[GK_PER];
+    double mine = 0.0;
+#pragma unroll
+    for (int i = 0; i < GK_PER; ++i) {
+        const int64_t k = kb + i;
+        loc[i] = k < n ? dt * (c[k - 1] + c[k]) / 2.0 : 0.0;
+        mine += loc[i];
+    }
+    // exclusive scan of the per-thread sums
+    double inc = mine;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const double u = __shfl_up_sync(0xffffffffu, inc, off);
         if (lane >= off) inc += u;
     }
-    if (lane == 31) warp_tot[w] = inc;
+    if (lane == 31) sh[w] = inc;
     __syncthreads();
-    if (w == 0) {
-        const double x = warp_tot[lane];
-        double xi = x;
+    double wbase = 0.0;
+    for (int i = 0; i < w; ++i) wbase += sh[i];
+    double I = before + wbase + (inc - mine);
+    if (blockIdx.x == 0 && t == 0) running[0] = 0.0;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const double u = __shfl_up_sync(0xffffffffu, xi, off);
-            if (lane >= off) xi += u;
+    for (int i = 0; i < GK_PER; ++i) {
+        const int64_t k = kb + i;
+        if (k < n) {
+            I += loc[i];
+            running[k] = prefactor * I;
         }
-        warp_tot[lane] = xi - x;
-    }
-    __syncthreads();
-    double I = warp_tot[w] + (inc - acc);
-    if (t == 0) running[0] = 0.0;
-    for (int64_t k = b; k < e; ++k) {
-        I += dt * (c[k - 1] + c[k]) / 2.0;
-        running[k] = prefactor * I;
     }
 }
 
@@ -256,7 +282,9 @@ cudaError_t upload_bytes(void *d_dst, const void *h_src, size_t nbytes, cudaStre
 
 cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
                                 double *d_running, cudaStream_t st) {
-    gk_integrate_kernel<<<1, GK_THREADS, 0, st>>>(d_c, n, dt, prefactor, d_running);
+    const int64_t blocks = n > 1 ? ceil_div(n - 1, GK_SPAN) : 1;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    gk_integrate_kernel<<<static_cast<unsigned>(blocks), GK_THREADS, 0, st>>>(d_c, n, dt, prefactor, d_running);
     return cudaGetLastError();
 }
 
