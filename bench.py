@@ -150,7 +150,7 @@ def gpu_identifier(torch, dev):
 # DRAM bytes (read + write) of one water-scale MSD launch of the tensor-core band kernel (FP16 x3),
 # from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
 # see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
-GRAM_WATER_TRAFFIC_BYTES = 8 * (1014.019e6 + 5.692e6)
+GRAM_WATER_TRAFFIC_BYTES = 8 * (982.338816e6 + 5.912576e6)
 
 
 def peaks():
@@ -617,7 +617,7 @@ def run_flux_workload(args, wl):
     u = updates(1, wl["T"], tm, 1) + wl["nshort"] * updates(1, wl["Tshort"], tm, 1)
     stream = torch.cuda.Stream(dev)
     res = {}
-    for method in (args.method, "plain"):
+    for method in ((args.method,) if args.no_plain_compare else (args.method, "plain")):
         outs = [torch.empty(tm + 1, dtype=torch.float64, device=dev) for _ in range(1 + wl["nshort"])]
         gks = [torch.empty(tm + 1, dtype=torch.float64, device=dev) for _ in range(1 + wl["nshort"])]
         items = [(1, x, tm, 1, o) for x, o in zip(xs, outs[1:])]
@@ -649,7 +649,7 @@ def run_flux_workload(args, wl):
         res[method] = (e0.elapsed_time(e1) / steps, clocks, outs[0].cpu().numpy())
         del ws_b, ws_l
     ms, clocks, c_tc = res[args.method]
-    p_ms, _, c_plain = res["plain"]
+    p_ms, _, c_plain = res.get("plain", (None, None, None))
     from paper_1708_08619_gb300 import shard
     ms = shard.max_over_ranks(ms)
     value = u * world / (ms / 1000.0)
@@ -660,10 +660,15 @@ def run_flux_workload(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.method,
             "data": "synthetic",
             "config": {"workload": wl["label"], "pairs_per_step": u, "plain_ms_per_step": p_ms,
-                       "speedup_vs_plain": p_ms / ms,
-                       "max_diff_tc_vs_plain_over_C0": float(np.max(np.abs(c_tc - c_plain)) / abs(c_plain[0])),
+                       "speedup_vs_plain": p_ms / ms if p_ms else None,
+                       "max_diff_tc_vs_plain_over_C0": (float(np.max(np.abs(c_tc - c_plain)) / abs(c_plain[0]))
+                                                        if c_plain is not None else None),
                        "l2": "long series 24 MB (fits L2); operand copies 0.2 GB"},
-            "clocks": clocks, "e2e": None, "gpu_launches": None,
+            "clocks": clocks, "e2e": None,
+            # per step: long series (row max, prep, Gram, reduction) + the batch (5 descriptor
+            # uploads, row max, prep, Gram, reduction) + one Green-Kubo integral per series
+            # (counted in the ncu launch list, profiles/gram_band_kernel_polyphase_flux.md)
+            "gpu_launches": (4 + 9 + 1 + wl["nshort"]) * args.steps if args.method != "plain" else None,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk.get("bf16_tflops", 1900.0),
                          "unit": "TFLOP/s", "frac": achieved / pk.get("bf16_tflops", 1900.0), "traffic": None,
                          "kernel": "gram_band_kernel (polyphase)",
