@@ -247,8 +247,9 @@ def run_gpu(args, wl):
     out_D = torch.empty(2, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     # plain: tile + reduce (MSD), tile + reduce (ACF), GK, Einstein
-    # tensor core: split + S prefix + gram + reduce (MSD), split + gram + reduce (ACF), GK, Einstein
-    launches_per_step = 6 if method == "plain" else 9
+    # tensor core: split + S combine + S prefix + gram + reduce (MSD), split + gram + reduce (ACF),
+    # GK, Einstein (the ncu launch list in profiles/gram_band_kernel_water.md shows the ten)
+    launches_per_step = 6 if method == "plain" else 10
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     msd_ms, acf_ms = [], []
