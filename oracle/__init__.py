@@ -6,7 +6,8 @@ links or calls anything here, and nothing here imports the CUDA library.
 
 The arithmetic lives in ``tcorr_oracle.c`` (plain FP64 loops following
 Eq. 5 / Algorithm 10 for the MSD, Eq. 4 / Algorithm 8 for the
-autocorrelation and its running Green-Kubo integral).  This module compiles it
+autocorrelation and its running Green-Kubo integral, and the same loop nest
+with the later factor taken from a second signal for the cross-correlation).  This module compiles it
 with gcc (no FMA contraction, no fast-math, so x86 and Arm give the same bits)
 and marshals numpy arrays through ctypes.
 
@@ -53,6 +54,8 @@ def load_library(path: str) -> ctypes.CDLL:
     vp = ctypes.c_void_p
     lib.oracle_corr.argtypes = [ctypes.c_int, vp, i64, i64, i64, vp, i64, vp, ctypes.c_int]
     lib.oracle_corr.restype = ctypes.c_int
+    lib.oracle_xcorr.argtypes = [vp, vp, i64, i64, i64, vp, i64, vp, ctypes.c_int]
+    lib.oracle_xcorr.restype = ctypes.c_int
     lib.oracle_gk_integrate.argtypes = [vp, i64, dbl, dbl, vp]
     lib.oracle_gk_integrate.restype = ctypes.c_int
     lib.oracle_einstein.argtypes = [vp, i64, dbl, ctypes.c_int, i64, i64, vp, vp]
@@ -103,6 +106,27 @@ def msd(x, tau_max=None, stride=1, lags=None, nthreads=None, lib=None):
 def acf(x, tau_max=None, stride=1, lags=None, nthreads=None, lib=None):
     """Autocorrelation <A(t0).A(t0+tau)>, the integrand of Eq. 4."""
     return corr(KIND_ACF, x, tau_max, stride, lags, nthreads, lib)
+
+
+def xcf(a, b, tau_max=None, stride=1, lags=None, nthreads=None, lib=None) -> np.ndarray:
+    """Cross-correlation <A(t0).B(t0+tau)> of a[T][N][3] and b[T][N][3] float32."""
+    lib = lib or _get_lib()
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    if a.ndim != 3 or a.shape[2] != 3 or b.shape != a.shape:
+        raise ValueError("a and b must both have shape [T][N][3]")
+    T, N, _ = a.shape
+    if lags is None:
+        if tau_max is None:
+            tau_max = T - 1
+        lags = np.arange(tau_max + 1, dtype=np.int64)
+    lags = np.ascontiguousarray(lags, dtype=np.int64)
+    out = np.zeros(lags.shape[0], dtype=np.float64)
+    rc = lib.oracle_xcorr(a.ctypes.data, b.ctypes.data, T, N, stride, lags.ctypes.data,
+                          lags.shape[0], out.ctypes.data, nthreads or default_threads())
+    if rc != 0:
+        raise ValueError(f"oracle_xcorr failed with code {rc}")
+    return out
 
 
 def gk_integrate(c, dt: float, prefactor: float = 1.0, lib=None) -> np.ndarray:

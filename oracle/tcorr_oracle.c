@@ -24,6 +24,12 @@
  *     C(tau)   = 1/(N n_o(tau)) * sum_i sum_{t0 in O(tau)} sum_c
  *                    A[t0][i][c] * A[t0+tau][i][c]
  *
+ *   Time cross-correlation of two signals A and B of the same shape (the
+ *   product of Algorithm 8 with the second factor taken from B):
+ *
+ *     X(tau)   = 1/(N n_o(tau)) * sum_i sum_{t0 in O(tau)} sum_c
+ *                    A[t0][i][c] * B[t0+tau][i][c]
+ *
  *   where O(tau) = { t0 = 0, s, 2s, ... : t0 + tau <= T-1 } (origin stride
  *   s >= 1, s = 1 is the paper's "all time origins") and
  *   n_o(tau) = floor((T-1-tau)/s) + 1 is its size.
@@ -53,7 +59,7 @@
 
 #define ORACLE_BLOCK 64
 
-enum { ORACLE_KIND_MSD = 0, ORACLE_KIND_ACF = 1 };
+enum { ORACLE_KIND_MSD = 0, ORACLE_KIND_ACF = 1, ORACLE_KIND_XCF = 2 };
 
 /* n_o(tau): number of origins t0 = 0, s, 2s, ... with t0 + tau <= T-1. */
 static int64_t n_origins(int64_t T, int64_t tau, int64_t s) {
@@ -63,6 +69,7 @@ static int64_t n_origins(int64_t T, int64_t tau, int64_t s) {
 
 typedef struct {
     const float *x;
+    const float *y;           /* kind XCF: B, the signal at the later time t0 + tau */
     int64_t T, N, s;
     const int64_t *lags;
     int64_t nlags;
@@ -73,24 +80,30 @@ typedef struct {
     pthread_mutex_t lock;
 } job_t;
 
-/* Per-lag sum over the atoms of one block, atoms in increasing order. */
+/* Per-lag sum over the atoms of one block, atoms in increasing order.
+ * traj holds 3T values (6T for XCF: A's, then B's). */
 static void do_block(job_t *J, int64_t b, double *traj) {
     const int64_t T = J->T, N = J->N, s = J->s;
     int64_t a0 = b * ORACLE_BLOCK, a1 = a0 + ORACLE_BLOCK;
     if (a1 > N) a1 = N;
     double *out = J->block_sums + b * J->nlags;
+    double *later = J->kind == ORACLE_KIND_XCF ? traj + 3 * T : traj;   /* signal at t0 + tau */
     for (int64_t l = 0; l < J->nlags; ++l) out[l] = 0.0;
     for (int64_t i = a0; i < a1; ++i) {
         /* copy atom i's trajectory to a contiguous buffer traj[t][c] (FP64) */
         for (int64_t t = 0; t < T; ++t)
             for (int c = 0; c < 3; ++c)
                 traj[3 * t + c] = (double)J->x[(t * N + i) * 3 + c];
+        if (J->kind == ORACLE_KIND_XCF)
+            for (int64_t t = 0; t < T; ++t)
+                for (int c = 0; c < 3; ++c)
+                    later[3 * t + c] = (double)J->y[(t * N + i) * 3 + c];
         for (int64_t l = 0; l < J->nlags; ++l) {
             const int64_t tau = J->lags[l];
             double acc = 0.0;
             for (int64_t t0 = 0; t0 + tau <= T - 1; t0 += s) {
                 const double *p = traj + 3 * t0;
-                const double *q = traj + 3 * (t0 + tau);
+                const double *q = later + 3 * (t0 + tau);
                 double term = 0.0;
                 for (int c = 0; c < 3; ++c) {
                     if (J->kind == ORACLE_KIND_MSD) {
@@ -109,7 +122,7 @@ static void do_block(job_t *J, int64_t b, double *traj) {
 
 static void *worker(void *arg) {
     job_t *J = (job_t *)arg;
-    double *traj = (double *)malloc(sizeof(double) * 3 * (size_t)J->T);
+    double *traj = (double *)malloc(sizeof(double) * (J->kind == ORACLE_KIND_XCF ? 6 : 3) * (size_t)J->T);
     if (!traj) return (void *)1;
     for (;;) {
         pthread_mutex_lock(&J->lock);
@@ -128,15 +141,16 @@ static void *worker(void *arg) {
  * out[l] = normalised result at lags[l].  Returns 0 on success, -1 on bad
  * arguments, -2 on allocation failure.
  */
-int oracle_corr(int kind, const float *x, int64_t T, int64_t N, int64_t s,
-                const int64_t *lags, int64_t nlags, double *out, int nthreads) {
+static int corr_run(int kind, const float *x, const float *y, int64_t T, int64_t N, int64_t s,
+                    const int64_t *lags, int64_t nlags, double *out, int nthreads) {
     if (!x || !lags || !out || T < 1 || N < 1 || s < 1 || nlags < 0) return -1;
-    if (kind != ORACLE_KIND_MSD && kind != ORACLE_KIND_ACF) return -1;
+    if (kind != ORACLE_KIND_MSD && kind != ORACLE_KIND_ACF && kind != ORACLE_KIND_XCF) return -1;
+    if (kind == ORACLE_KIND_XCF && !y) return -1;
     for (int64_t l = 0; l < nlags; ++l)
         if (lags[l] < 0 || lags[l] > T - 1) return -1;
     if (nthreads < 1) nthreads = 1;
     job_t J;
-    J.x = x; J.T = T; J.N = N; J.s = s; J.lags = lags; J.nlags = nlags;
+    J.x = x; J.y = y; J.T = T; J.N = N; J.s = s; J.lags = lags; J.nlags = nlags;
     J.kind = kind;
     J.nblocks = (N + ORACLE_BLOCK - 1) / ORACLE_BLOCK;
     J.next_block = 0;
@@ -169,6 +183,21 @@ done:
     pthread_mutex_destroy(&J.lock);
     free(J.block_sums);
     return rc;
+}
+
+int oracle_corr(int kind, const float *x, int64_t T, int64_t N, int64_t s,
+                const int64_t *lags, int64_t nlags, double *out, int nthreads) {
+    if (kind == ORACLE_KIND_XCF) return -1;
+    return corr_run(kind, x, NULL, T, N, s, lags, nlags, out, nthreads);
+}
+
+/*
+ * oracle_xcorr: cross-correlation X(tau) of a (at the origin t0) and b (at
+ * t0 + tau), both [T][N][3] float32, at the listed lags.
+ */
+int oracle_xcorr(const float *a, const float *b, int64_t T, int64_t N, int64_t s,
+                 const int64_t *lags, int64_t nlags, double *out, int nthreads) {
+    return corr_run(ORACLE_KIND_XCF, a, b, T, N, s, lags, nlags, out, nthreads);
 }
 
 /* Running Green-Kubo integral (Eq. 4, trapezoid): running[0..n-1]. */

@@ -291,9 +291,77 @@ def pin_einstein_vs_green_kubo(lib):
     assert abs(d_e / d_gk - 1) < 0.05, (d_e, d_gk)
 
 
+# ------------------------------------------------------- cross-correlation
+
+def _brute_cross(a, b, tau_max, s):
+    """sum over origins t0 (multiples of s) of a[t0] . b[t0 + tau], over every
+    ordered frame pair, binned by lag and averaged over atoms and origins."""
+    a = a.astype(np.float64)
+    b = b.astype(np.float64)
+    T, N, _ = a.shape
+    sums = np.zeros(tau_max + 1)
+    counts = np.zeros(tau_max + 1)
+    for t0 in range(0, T, s):
+        for t1 in range(t0, min(T, t0 + tau_max + 1)):
+            sums[t1 - t0] += float((a[t0] * b[t1]).sum())
+            counts[t1 - t0] += N
+    return sums / counts
+
+
+def pin_xcf_brute_force(lib):
+    rng = np.random.default_rng(31)
+    for T in (1, 2, 5, 9):
+        for N in (1, 3):
+            a = rng.normal(size=(T, N, 3)).astype(np.float32)
+            b = rng.normal(size=(T, N, 3)).astype(np.float32)
+            for s in (1, 2, T + 1):
+                for tau_max in range(T):
+                    _close(oracle.xcf(a, b, tau_max, s, lib=lib), _brute_cross(a, b, tau_max, s), 1e-13, 1e-15,
+                           what=f"brute xcf T={T} N={N} s={s} tm={tau_max}")
+
+
+def pin_xcf_fft(lib):
+    """sum_t a[t] b[t+tau] per column = irfft(conj(rfft a) rfft b) (zero padded)."""
+    rng = np.random.default_rng(32)
+    T, N = 80, 4
+    a = rng.uniform(-1.0, 1.0, size=(T, N, 3)).astype(np.float32)
+    b = rng.uniform(-1.0, 1.0, size=(T, N, 3)).astype(np.float32)
+    n = 1 << (2 * T - 1).bit_length()
+    fa = np.fft.rfft(a.astype(np.float64).reshape(T, -1), n=n, axis=0)
+    fb = np.fft.rfft(b.astype(np.float64).reshape(T, -1), n=n, axis=0)
+    lagged = np.fft.irfft(np.conj(fa) * fb, n=n, axis=0)[:T].sum(axis=1)
+    want = lagged / (N * (T - np.arange(T)))
+    _close(oracle.xcf(a, b, T - 1, lib=lib), want, 1e-10, 1e-13, what="xcf fft")
+
+
+def pin_xcf_closed_forms(lib):
+    """A constant (p) and B linear in time (v t), dyadic so every product is
+    exact: X(tau) = <p.v> (tau + s (n_o - 1) / 2); the reverse order gives
+    <p.v> s (n_o - 1) / 2, so the two signals' roles are pinned.  And X(A, A)
+    is the autocorrelation, bit for bit."""
+    rng = np.random.default_rng(33)
+    T, N = 60, 5
+    p = (rng.integers(-64, 64, size=(N, 3)) / 64.0).astype(np.float32)
+    v = (rng.integers(-64, 64, size=(N, 3)) / 1024.0).astype(np.float32)
+    a = np.repeat(p[None], T, axis=0)
+    t = np.arange(T, dtype=np.float32)[:, None, None]
+    b = (v[None] * t).astype(np.float32)
+    pv = float((p.astype(np.float64) * v.astype(np.float64)).sum()) / N
+    for s in (1, 3):
+        tau = np.arange(T)
+        n_o = (T - 1 - tau) // s + 1
+        _close(oracle.xcf(a, b, T - 1, s, lib=lib), pv * (tau + s * (n_o - 1) / 2.0), 1e-13, 1e-14,
+               what=f"xcf const x linear s={s}")
+        _close(oracle.xcf(b, a, T - 1, s, lib=lib), pv * (s * (n_o - 1) / 2.0), 1e-13, 1e-14,
+               what=f"xcf linear x const s={s}")
+    x = rng.normal(size=(30, 6, 3)).astype(np.float32)
+    if not np.array_equal(oracle.xcf(x, x, 29, 2, lib=lib), oracle.acf(x, 29, 2, lib=lib)):
+        raise AssertionError("xcf(A, A) differs from acf(A)")
+
+
 ALL_PINS = [
     pin_hand_worked, pin_brute_force, pin_lag_subset, pin_fft, pin_constant_velocity,
     pin_zero_lag, pin_single_origin, pin_invariants, pin_stride_split,
     pin_gk_closed_forms, pin_einstein_exact, pin_random_walk, pin_ou,
-    pin_einstein_vs_green_kubo,
+    pin_einstein_vs_green_kubo, pin_xcf_brute_force, pin_xcf_fft, pin_xcf_closed_forms,
 ]

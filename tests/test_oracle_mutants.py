@@ -24,13 +24,16 @@ MUTANTS = [
     ("component_dropped", "for (int c = 0; c < 3; ++c) {", "for (int c = 0; c < 2; ++c) {", 0),
     ("n_origins_off_by_one", "return (T - 1 - tau) / s + 1;", "return (T - tau) / s + 1;", 0),
     ("per_component_norm", "out[l] = total / ((double)N *", "out[l] = total / ((double)(3 * N) *", 0),
-    ("origin_not_added", "const double *q = traj + 3 * (t0 + tau);", "const double *q = traj + 3 * tau;", 0),
+    ("origin_not_added", "const double *q = later + 3 * (t0 + tau);", "const double *q = later + 3 * tau;", 0),
     ("layout_transposed", "J->x[(t * N + i) * 3 + c]", "J->x[(i * T + t) * 3 + c]", 0),
     ("atom_sum_overwritten", "out[l] += acc;", "out[l] = acc;", 0),
     ("trapezoid_half_dropped", "I += dt * (c[k - 1] + c[k]) / 2.0;", "I += dt * (c[k - 1] + c[k]);", 0),
     ("trapezoid_right_point", "I += dt * (c[k - 1] + c[k]) / 2.0;", "I += dt * (c[k] + c[k]) / 2.0;", 0),
     ("einstein_no_2", "*D_slope = (sxy / sxx) / (2.0 * dim);", "*D_slope = (sxy / sxx) / (double)dim;", 0),
     ("einstein_time_axis", "const double dx = (double)k * dt - xbar;", "const double dx = (double)k - xbar;", 0),
+    ("xcf_second_signal_ignored", "later[3 * t + c] = (double)J->y[", "later[3 * t + c] = (double)J->x[", 0),
+    ("xcf_time_roles_swapped", "const double *p = traj + 3 * t0;\n                const double *q = later + 3 * (t0 + tau);",
+     "const double *p = later + 3 * t0;\n                const double *q = traj + 3 * (t0 + tau);", 0),
 ]
 
 
