@@ -122,6 +122,27 @@ int tcorr_acf(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s
               int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * Time cross-correlation of two signals of the same shape:
+ *   d_out[tau] = 1/(N n_o(tau)) sum_i sum_{t0} A[t0][i] . B[t0+tau][i],
+ *   tau = 0 .. tau_max (the product of Algorithm 8 with the later factor taken
+ *   from B; for negative lags swap the arguments).  With A = B it is
+ *   tcorr_acf.  Per-atom pairs give cross terms such as velocity-force or
+ *   position-velocity correlations; with N = 1 and A, B summed over the atoms
+ *   of two species (or weighted by charge) it gives the collective
+ *   cross-correlations of Green-Kubo transport (interdiffusion, charge
+ *   current).  The paper computes autocorrelations only; this is the same loop
+ *   nest with two signals.  Both methods use the band form for every K (the
+ *   small-K polyphase form of tcorr_acf is not used here).
+ * d_a, d_b: [T][N][3] float32, 4-byte aligned; d_out: tau_max+1 doubles,
+ * 8-byte aligned; d_ws: tcorr_xcf_workspace_size(...) bytes (the tensor-core
+ * methods keep split copies of both signals), 256-byte aligned.
+ * Errors: as tcorr_msd.
+ */
+size_t tcorr_xcf_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method);
+int tcorr_xcf(const float *d_a, const float *d_b, int64_t T, int64_t N, int64_t tau_max,
+              int64_t stride, int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Running Green-Kubo integral of Eq. 4, trapezoid rule on the frame grid
  * (the quadrature loop closing Algorithms 8/9, done on the GPU here):
  *   d_running[0] = 0,

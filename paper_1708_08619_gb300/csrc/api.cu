@@ -21,15 +21,9 @@ int plain_tile_bf();
 int plain_tile_wp();
 
 // Tensor-core path (gram_tc.cu).
-size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-                           const Window *w = nullptr);
 size_t gram_batch_workspace_size(const tcorr_instance *items, int count, int method);
 int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_ws, size_t ws_bytes,
                    cudaStream_t st);
-int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
-             int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st,
-             const Window *w = nullptr);
-bool gram_method_available(int method);
 int status_poll_and_clear(cudaStream_t st);
 int selftest_timeout(cudaStream_t st);
 
@@ -99,13 +93,13 @@ int resolve_method(int method, int64_t T, int64_t N, int64_t tau_max, int64_t s)
 
 // Plain FP32 path for one trajectory, or one window of it (w != nullptr).
 int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
-              void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w) {
+              void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w, const float *d_y) {
     BandPlan p = make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg, kMinItems);
     if (w) cap_origins(&p, w->orig_cap);
     const size_t need = align256(sizeof(double) * static_cast<size_t>(p.n_items) * p.WP);
     if (ws_bytes < need || (need > 0 && !d_ws)) return TCORR_EWORKSPACE;
     double *partial = static_cast<double *>(d_ws);
-    cudaError_t e = launch_plain_tiles(kind, d_x, p, partial, st);
+    cudaError_t e = launch_plain_tiles(kind, d_x, p, partial, st, d_y);
     if (e != cudaSuccess) return cuda_fail(e, "plain_tile_kernel launch");
     FinalizeArgs fa{0, nullptr, 0};
     e = launch_lag_reduce(p, partial, fa, d_out, st, w);
@@ -299,6 +293,21 @@ int batch_run_graph(const tcorr_instance *items, int count, int m, void *d_ws, s
 
 // The plain path's plan and size check, shared with the fixed-scratch entry
 // point so that both produce bit-identical results for the same arguments.
+// Cross-correlation: products of d_a at the origin and d_b at the later frame,
+// band form on either path (no polyphase: its operand copies hold one signal).
+int run_xcf(const float *d_a, const float *d_b, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+            double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!d_a || !d_b || !d_out) return TCORR_EINVAL;
+    if (!valid_sizes(T, N, tau_max, s) || !known_method(method)) return TCORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_a) & 3u) || (reinterpret_cast<uintptr_t>(d_b) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_out) & 7u) || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+        return TCORR_EALIGN;
+    const int m = resolve_method(method, T, N, tau_max, s);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (m != TCORR_PLAIN) return gram_run(2, d_a, T, N, tau_max, s, m, d_out, d_ws, ws_bytes, st, nullptr, d_b);
+    return plain_run(2, d_a, T, N, tau_max, s, d_out, d_ws, ws_bytes, st, nullptr, d_b);
+}
+
 BandPlan plain_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     return make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg, kMinItems);
 }
@@ -328,6 +337,18 @@ int tcorr_msd(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s
 int tcorr_acf(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method,
               double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
     return run_corr(1, d_x, T, N, tau_max, stride, method, d_out, d_ws, ws_bytes, stream);
+}
+
+size_t tcorr_xcf_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method) {
+    if (!valid_sizes(T, N, tau_max, stride) || !known_method(method)) return 0;
+    const int m = resolve_method(method, T, N, tau_max, stride);
+    if (m == TCORR_PLAIN) return plain_workspace(T, N, tau_max, stride);
+    return gram_workspace_size(T, N, tau_max, stride, m, nullptr, 2);
+}
+
+int tcorr_xcf(const float *d_a, const float *d_b, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+              int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    return run_xcf(d_a, d_b, T, N, tau_max, stride, method, d_out, d_ws, ws_bytes, stream);
 }
 
 int gk_integrate(const double *d_c, int64_t n, double dt, double prefactor, double *d_running,

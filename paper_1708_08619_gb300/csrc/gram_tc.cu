@@ -103,6 +103,7 @@ struct GramArgs {
     int64_t kb_per_item;    // K-blocks per work item
     const float *inv_scale; // 2^-e per frame (FP16): [group][scale_stride] (band) or [phase] (polyphase)
     int64_t scale_stride;   // band: T_pad (one row of scales per K-group); polyphase: 0
+    const float *inv_scale_b;   // scales of the frame (column) operand: B's for a cross-correlation
     double *partial;        // [n_items][WPG]
     int b3d;                // B map is 3-D (K, residue, frame index) when s > 1
     int sub_kb;             // K-blocks per accumulation sub-chain
@@ -648,10 +649,11 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             float rs = 1.f;
             if (PREC == P_FP16) {
                 const int64_t nscale = a.mode == 0 ? a.T : 3 * BO;
-                const float *isc = a.inv_scale + (I.kb0 / a.kb_per_item) * a.scale_stride;
+                const int64_t gofs = (I.kb0 / a.kb_per_item) * a.scale_stride;
+                const float *isc = a.inv_scale + gofs, *iscb = a.inv_scale_b + gofs;
                 for (int j = et; j < BF; j += 32 * NEPI) {
                     const int64_t f = I.sb0 + j * I.sstr;
-                    cs[j] = f < nscale ? isc[f] : 1.f;
+                    cs[j] = f < nscale ? iscb[f] : 1.f;
                 }
                 rs = (row < I.a_rows) ? isc[I.sa0 + row * I.sstr] : 1.f;
                 named_bar_sync(1, 32 * NEPI);
@@ -1285,6 +1287,8 @@ struct GramLayout {
     bool poly;                      // polyphase layout (small K, stride 1)
     int64_t P, Pp, nq, Kprime, Kalloc;
     size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, off_counter, total;
+    bool cross = false;             // cross-correlation: B operand from a second signal
+    size_t off_bh = 0, off_bl = 0, off_scale_b = 0;
 };
 
 bool method_prec(int method, int *prec, bool *x4) {
@@ -1366,7 +1370,8 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->esize = L->prec == P_TF32 ? 4 : 2;
     L->bke = L->prec == P_TF32 ? 16 : 32;
     const int64_t K = 3 * N;
-    L->poly = !w && use_polyphase(T, N, tau_max, s);
+    L->cross = kind == 2;
+    L->poly = !w && !L->cross && use_polyphase(T, N, tau_max, s);
     if (L->poly) return make_poly_layout(T, N, tau_max, method, kind, L);
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
@@ -1405,6 +1410,11 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->off_xh = take(size_t(L->T_pad) * L->Kp * L->esize);
     L->off_xl = take(size_t(L->T_pad) * L->Kp * L->esize);
     L->off_scale = take(size_t(L->p.n_groups) * L->T_pad * sizeof(float));
+    if (L->cross) {
+        L->off_bh = take(size_t(L->T_pad) * L->Kp * L->esize);
+        L->off_bl = take(size_t(L->T_pad) * L->Kp * L->esize);
+        L->off_scale_b = take(size_t(L->p.n_groups) * L->T_pad * sizeof(float));
+    }
     L->off_S = take(kind == 0 ? size_t(L->p.n_groups) * T * sizeof(double) : 0);
     L->off_prefix = take(kind == 0 ? size_t(L->p.n_res) * L->pstride * sizeof(double) : 0);
     L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
@@ -1508,6 +1518,7 @@ int encode_maps(const GramLayout &L, uint8_t *base, int64_t s, CUtensorMap *maps
                                    : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     void *bases[2] = {base + L.off_xh, base + L.off_xl};
+    void *bbases[2] = {base + (L.cross ? L.off_bh : L.off_xh), base + (L.cross ? L.off_bl : L.off_xl)};
     const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kp * L.esize);
     const cuuint32_t es2[2] = {1, 1};
     for (int h = 0; h < 2; ++h) {
@@ -1528,14 +1539,14 @@ int encode_maps(const GramLayout &L, uint8_t *base, int64_t s, CUtensorMap *maps
                 const cuuint64_t strB[2] = {rowb, rowb * static_cast<cuuint64_t>(s)};
                 const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), 1, rows};
                 const cuuint32_t es3[3] = {1, 1, 1};
-                rb = encode(mB, dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                rb = encode(mB, dt, 3, bbases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             } else {
                 const cuuint64_t dimB[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.n_k)};
                 const cuuint64_t strB[1] = {rowb};
                 const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(L.bke), rows};
-                rb = encode(mB, dt, 2, bases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                rb = encode(mB, dt, 2, bbases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             }
@@ -1561,6 +1572,7 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
     ga.kb_per_item = L.kseg / L.bke;
     ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
     ga.scale_stride = L.T_pad;
+    ga.inv_scale_b = reinterpret_cast<const float *>(base + (L.cross ? L.off_scale_b : L.off_scale));
     ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = s > 1 ? 1 : 0;
     ga.sub_kb = L.sub_kb;
@@ -1697,6 +1709,7 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     ga.kb_total = ceil_div(L.Kprime, L.bke);
     ga.kb_per_item = L.kseg / L.bke;
     ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
+    ga.inv_scale_b = ga.inv_scale;
     ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = 2;
     ga.sub_kb = L.sub_kb;
@@ -1786,16 +1799,17 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
 
 // Workspace bound: the MSD layout (a superset of the ACF one) with the chosen
 // parameters, and with the shortest candidate work item when tuning may run.
-size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, const Window *w) {
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, const Window *w,
+                           int kind) {
     GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, 0, &L, w)) return 0;
+    if (!make_layout(T, N, tau_max, s, method, kind, &L, w)) return 0;
     size_t need = L.total;
     if (!w && tune_mode() != 0) {
         const TuneChoice shortest{tune_min_kseg(), kSubKb};
         const TuneChoice *prev = get_tune_override();
         set_tune_override(&shortest);
         GramLayout Ls;
-        if (make_layout(T, N, tau_max, s, method, 0, &Ls) && Ls.total > need) need = Ls.total;
+        if (make_layout(T, N, tau_max, s, method, kind, &Ls) && Ls.total > need) need = Ls.total;
         set_tune_override(prev);
     }
     return need;
@@ -1816,8 +1830,10 @@ bool gram_method_available(int method) {
 
 namespace {
 
+// kind 0 MSD, 1 ACF, 2 cross-correlation of d_x (origins) with d_y (later frames).
 int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-                  double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w = nullptr) {
+                  double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w = nullptr,
+                  const float *d_y = nullptr) {
     GramLayout L;
     if (!make_layout(T, N, tau_max, s, method, kind, &L, w)) return TCORR_EUNSUPPORTED;
     if (ws_bytes < L.total || !d_ws) return TCORR_EWORKSPACE;
@@ -1826,14 +1842,22 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
     if (L.poly) return poly_run(kind, d_x, L, ws, d_out, num_sms, st);
 
-    const SplitDesc q = split_desc(kind, d_x, L, ws, 0);
-    cudaError_t e;
-    switch (L.prec) {
-        case P_FP16: e = launch_split<P_FP16>(q, st); break;
-        case P_BF16: e = launch_split<P_BF16>(q, st); break;
-        default: e = launch_split<P_TF32>(q, st); break;
-    }
+    auto split = [&](const SplitDesc &q) {
+        switch (L.prec) {
+            case P_FP16: return launch_split<P_FP16>(q, st);
+            case P_BF16: return launch_split<P_BF16>(q, st);
+            default: return launch_split<P_TF32>(q, st);
+        }
+    };
+    cudaError_t e = split(split_desc(kind == 2 ? 1 : kind, d_x, L, ws, 0));
     if (e != cudaSuccess) return cuda_fail(e, "split_kernel launch");
+    if (kind == 2) {                  // B: its own hi/lo copies and scales
+        SplitDesc qb = split_desc(1, d_y, L, ws, 0);
+        qb.Xh = ws + L.off_bh;
+        qb.Xl = ws + L.off_bl;
+        qb.inv_scale = reinterpret_cast<float *>(ws + L.off_scale_b);
+        if ((e = split(qb)) != cudaSuccess) return cuda_fail(e, "split_kernel launch (B)");
+    }
     if (kind == 0) {
         double *S = reinterpret_cast<double *>(ws + L.off_S);
         if (L.p.n_groups > 1)
@@ -1851,10 +1875,10 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     if (e != cudaSuccess) return cuda_fail(e, "work-item counter reset");
     const int grid = static_cast<int>(L.p.n_items < num_sms ? L.p.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
-        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st, kind); break;
-        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st, kind); break;
-        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st, kind); break;
-        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st, kind); break;
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st, kind & 1); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(maps, ga, grid, st, kind & 1); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(maps, ga, grid, st, kind & 1); break;
+        default: e = launch_gram<P_TF32, false>(maps, ga, grid, st, kind & 1); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel launch");
     e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st, w);
@@ -1864,7 +1888,8 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
 
 // Times every tuning candidate on the stream (synchronising) and keeps the fastest.
 int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
-              int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, TuneChoice *best) {
+              int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, TuneChoice *best,
+              const float *d_y) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return TCORR_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1875,10 +1900,10 @@ int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int
     int rc = TCORR_OK;
     for (const TuneChoice &c : tune_candidates()) {
         set_tune_override(&c);
-        rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);   // warm-up
+        rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, nullptr, d_y);   // warm-up
         if (rc == TCORR_OK) {
             cudaEventRecord(e0, st);
-            rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);
+            rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, nullptr, d_y);
             cudaEventRecord(e1, st);
         }
         set_tune_override(nullptr);
@@ -1903,8 +1928,8 @@ int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int
 }  // namespace
 
 int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w) {
-    if (w) return gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, w);
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w, const float *d_y) {
+    if (w) return gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, w, d_y);
     const int mode = tune_mode();
     if (mode != 0 && !env_kseg() && !env_sub_kb()) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1912,16 +1937,18 @@ int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
             const std::string key = tune_key(method, kind, 3 * N, tau_max, T, s);
             TuneChoice c;
             if (mode == 2 || !tune_lookup(key, &c)) {
-                const int rc = gram_tune(key, kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, &c);
+                const int rc = gram_tune(key, kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, &c,
+                                         d_y);
                 if (rc != TCORR_OK) return rc;
             }
             set_tune_override(&c);
-            const int rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);
+            const int rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, nullptr,
+                                         d_y);
             set_tune_override(nullptr);
             return rc;
         }
     }
-    return gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st);
+    return gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, nullptr, d_y);
 }
 
 // Whole batch: one batched prep launch, one batched S-prefix launch, Gram

@@ -34,7 +34,8 @@ constexpr size_t SMEM_BYTES = sizeof(float) * (2 * STAGES * BK * LDS + 64 * PLD)
 
 // One instance of the plain path (also one entry of a batch).
 struct PlainArgs {
-    const float *x;
+    const float *x;         // origin rows (A of a cross-correlation)
+    const float *xb;        // partner-frame rows: B of a cross-correlation, else x
     int64_t T, K, s, tau_max, n_orig;
     int64_t n_res, n_rows, n_cols, kseg, segs_per_item;
     double *partial;        // [n_items][WP] of this instance
@@ -98,7 +99,7 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
     const int64_t oA = o0 + lrow, kB = k0 + lrow;
     const bool vA = oA < a.n_orig, vB = kB < n_rho;
     const float *gA = a.x + (vA ? oA * a.s * a.K : 0);
-    const float *gB = a.x + (vB ? (rho + kB * a.s) * a.K : 0);
+    const float *gB = a.xb + (vB ? (rho + kB * a.s) * a.K : 0);
     const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
 
     const int64_t kbeg = g * a.segs_per_item * a.kseg;
@@ -230,9 +231,10 @@ __global__ void __launch_bounds__(NT, 2) plain_tile_batch_kernel(const PlainArgs
 PlainArgs plain_args(int kind, const float *d_x, const BandPlan &p, double *partial, int64_t item_begin);
 
 cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, double *partial,
-                               cudaStream_t st) {
+                               cudaStream_t st, const float *d_xb) {
     if (p.BO != BO || p.BF != BF || p.WP != WP) return cudaErrorInvalidValue;
-    const PlainArgs a = plain_args(kind, d_x, p, partial, 0);
+    PlainArgs a = plain_args(kind == 2 ? 1 : kind, d_x, p, partial, 0);
+    if (kind == 2) a.xb = d_xb;          // cross-correlation: products, B at the later frame
     if (p.n_items <= 0) return cudaSuccess;
     if (p.n_items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
@@ -257,6 +259,7 @@ cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, do
 PlainArgs plain_args(int kind, const float *d_x, const BandPlan &p, double *partial, int64_t item_begin) {
     PlainArgs a;
     a.x = d_x;
+    a.xb = d_x;
     a.T = p.T;
     a.K = p.K;
     a.s = p.s;

@@ -24,15 +24,6 @@
 
 namespace tcorr {
 
-size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, const Window *w);
-int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
-             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w);
-bool gram_method_available(int method);
-int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
-              void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w);
-size_t plain_window_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s, int64_t orig_cap);
-bool corr_sizes_valid(int64_t T, int64_t N, int64_t tau_max, int64_t s);
-
 namespace {
 
 // Origins per window when the caller passes 0: four halos' worth, at least

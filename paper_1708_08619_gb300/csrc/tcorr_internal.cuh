@@ -75,6 +75,21 @@ struct Window {
 // Restricts a plan to its first `cap` origins (row tiles and items shrink).
 void cap_origins(BandPlan *p, int64_t cap);
 
+// Whole-path runs, kind 0 MSD, 1 ACF, 2 cross-correlation of d_x (at the
+// origin) with d_y (at the later frame).  Tensor-core path (gram_tc.cu):
+size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+                           const Window *w = nullptr, int kind = 0);
+int gram_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+             double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w = nullptr,
+             const float *d_y = nullptr);
+bool gram_method_available(int method);
+// Plain FP32 path (api.cu):
+int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
+              void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w = nullptr,
+              const float *d_y = nullptr);
+size_t plain_window_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s, int64_t orig_cap);
+bool corr_sizes_valid(int64_t T, int64_t N, int64_t tau_max, int64_t s);
+
 // Maps a failed CUDA call to TCORR_ECUDA; with TCORR_VERBOSE set in the
 // environment it also prints the call site and CUDA's error string.
 inline int cuda_fail(cudaError_t e, const char *what) {
@@ -108,9 +123,10 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // ------------------------------------------------------------------ kernels
 // Plain FP32 path: per-item per-offset partial sums (double) into `partial`
-// ([n_items][WP]).  kind 0 = MSD (differences), 1 = ACF (products).
+// ([n_items][WP]).  kind 0 = MSD (differences), 1 = ACF (products), 2 =
+// cross-correlation (products of d_x at the origin and d_xb at the later frame).
 cudaError_t launch_plain_tiles(int kind, const float *d_x, const BandPlan &p, double *partial,
-                               cudaStream_t st);
+                               cudaStream_t st, const float *d_xb = nullptr);
 // Batch of plain instances: d_descs holds one PlainArgs (plain.cu) per
 // instance, plain_args_size() bytes each, written by plain_args_write.
 size_t plain_args_size();

@@ -49,6 +49,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = [vp, i64, i64, i64, i64, ci, vp, vp, sz, vp]
         f.restype = ci
+    lib.tcorr_xcf_workspace_size.argtypes = [i64, i64, i64, i64, ci]
+    lib.tcorr_xcf_workspace_size.restype = sz
+    lib.tcorr_xcf.argtypes = [vp, vp, i64, i64, i64, i64, ci, vp, vp, sz, vp]
+    lib.tcorr_xcf.restype = ci
     lib.gk_integrate.argtypes = [vp, i64, dbl, dbl, vp, vp]
     lib.gk_integrate.restype = ci
     lib.einstein_slope.argtypes = [vp, i64, dbl, ci, i64, i64, vp, vp]
@@ -143,6 +147,33 @@ def tcorr_msd(x, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, 
 def tcorr_acf(x, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, stream=None):
     """<A(t0).A(t0+tau)>, tau = 0..tau_max, of A[T][N][3] (Eq. 4 integrand)."""
     return _corr("tcorr_acf", x, tau_max, stride, method, out, ws, stream)
+
+
+def tcorr_xcf_workspace_size(T: int, N: int, tau_max: int, stride: int = 1, method=AUTO) -> int:
+    return int(load().tcorr_xcf_workspace_size(T, N, tau_max, stride, _method(method)))
+
+
+def tcorr_xcf(a, b, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, stream=None):
+    """<A(t0).B(t0+tau)>, tau = 0..tau_max, of A and B [T][N][3] (same shape)."""
+    torch = _torch()
+    _check_traj(a)
+    _check_traj(b)
+    if a.shape != b.shape:
+        raise TypeError("a and b must have the same shape")
+    T, N, _ = a.shape
+    m = _method(method)
+    if out is None:
+        out = torch.empty(tau_max + 1, dtype=torch.float64, device=a.device)
+    need = tcorr_xcf_workspace_size(T, N, tau_max, stride, m)
+    if ws is None:
+        ws = _alloc_ws(need, a.device)
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = load().tcorr_xcf(a.data_ptr(), b.data_ptr(), T, N, tau_max, stride, m, out.data_ptr(), ws_ptr, ws_bytes,
+                          _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_xcf")
+    return out
 
 
 def gk_integrate(c, dt: float, prefactor: float = 1.0, out=None, stream=None):
