@@ -87,7 +87,19 @@ typedef enum {
     TCORR_TC_BF16X3 = 2,
     TCORR_TC_BF16X4 = 3,
     TCORR_TC_FP16X3 = 4,     /* FP16 hi/lo with a power-of-two scale */
-    TCORR_AUTO = 5           /* the library picks (tensor-core when it can) */
+    TCORR_AUTO = 5,          /* the library picks (tensor-core when it can) */
+    /* FFT route (not in the paper): per column, the lag sums up to tau_max are
+       the inverse transform of the (cross) power spectrum of the column
+       zero-padded to L >= T + tau_max (FP64 transforms by cuFFT, FP64 sums
+       over columns; stride s uses the origin-masked signal on one side).
+       Cost O(K T log T) instead of O(K T tau_max): the choice when tau_max is
+       a large fraction of T.  Plans are created once per shape and device
+       (cuFFT keeps its own small plan data); the work area is the caller's
+       workspace, and tcorr_workspace_size makes CUDA calls for this method
+       (it returns 0 without a device).  Accuracy target: 1e-5 relative to
+       C(0) or MSD(tau_max).  Not available in tcorr_batch or the streamed
+       calls. */
+    TCORR_FFT = 6
 } tcorr_method;
 
 /*

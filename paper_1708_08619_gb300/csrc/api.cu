@@ -72,7 +72,7 @@ bool valid_sizes(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     return true;
 }
 
-bool known_method(int m) { return m >= TCORR_PLAIN && m <= TCORR_AUTO; }
+bool known_method(int m) { return (m >= TCORR_PLAIN && m <= TCORR_AUTO) || m == TCORR_FFT; }
 
 size_t plain_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     const BandPlan p = make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg,
@@ -124,6 +124,7 @@ int run_corr(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, 
         return TCORR_EALIGN;
     const int m = resolve_method(method, T, N, tau_max, s);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (m == TCORR_FFT) return fft_run(kind, d_x, T, N, tau_max, s, d_out, d_ws, ws_bytes, st);
     if (m != TCORR_PLAIN)
         return gram_run(kind, d_x, T, N, tau_max, s, m, d_out, d_ws, ws_bytes, st);
     return plain_run(kind, d_x, T, N, tau_max, s, d_out, d_ws, ws_bytes, st, nullptr);
@@ -304,6 +305,7 @@ int run_xcf(const float *d_a, const float *d_b, int64_t T, int64_t N, int64_t ta
         return TCORR_EALIGN;
     const int m = resolve_method(method, T, N, tau_max, s);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (m == TCORR_FFT) return fft_run(2, d_a, T, N, tau_max, s, d_out, d_ws, ws_bytes, st, d_b);
     if (m != TCORR_PLAIN) return gram_run(2, d_a, T, N, tau_max, s, m, d_out, d_ws, ws_bytes, st, nullptr, d_b);
     return plain_run(2, d_a, T, N, tau_max, s, d_out, d_ws, ws_bytes, st, nullptr, d_b);
 }
@@ -326,6 +328,7 @@ size_t tcorr_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t strid
     if (!valid_sizes(T, N, tau_max, stride) || !known_method(method)) return 0;
     const int m = resolve_method(method, T, N, tau_max, stride);
     if (m == TCORR_PLAIN) return plain_workspace(T, N, tau_max, stride);
+    if (m == TCORR_FFT) return fft_workspace_size(T, N, tau_max, stride, 0);
     return gram_workspace_size(T, N, tau_max, stride, m);
 }
 
@@ -343,6 +346,7 @@ size_t tcorr_xcf_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s
     if (!valid_sizes(T, N, tau_max, stride) || !known_method(method)) return 0;
     const int m = resolve_method(method, T, N, tau_max, stride);
     if (m == TCORR_PLAIN) return plain_workspace(T, N, tau_max, stride);
+    if (m == TCORR_FFT) return fft_workspace_size(T, N, tau_max, stride, 2);
     return gram_workspace_size(T, N, tau_max, stride, m, nullptr, 2);
 }
 

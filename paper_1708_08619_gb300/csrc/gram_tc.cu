@@ -1815,6 +1815,12 @@ size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int
     return need;
 }
 
+cudaError_t launch_s_prefix(const double *S, int64_t T, int64_t s, int64_t n_res, int64_t pstride,
+                            double *prefix, cudaStream_t st) {
+    s_prefix_kernel<<<static_cast<unsigned>(n_res), PFX_THREADS, 0, st>>>(S, T, 1, s, pstride, prefix);
+    return cudaGetLastError();
+}
+
 size_t gram_batch_workspace_size(const tcorr_instance *items, int count, int method) {
     BatchLayout B;
     if (!make_batch_layout(items, count, method, &B)) return 0;

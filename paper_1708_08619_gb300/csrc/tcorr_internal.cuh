@@ -89,6 +89,13 @@ int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max,
               const float *d_y = nullptr);
 size_t plain_window_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s, int64_t orig_cap);
 bool corr_sizes_valid(int64_t T, int64_t N, int64_t tau_max, int64_t s);
+// FFT route (fft.cu); its sizes come from cuFFT plans, so it needs a device.
+size_t fft_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int kind);
+int fft_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
+            void *d_ws, size_t ws_bytes, cudaStream_t st, const float *d_y = nullptr);
+// prefix[rho][j] = sum_{j' < j} S(rho + j' s) for the residues rho < n_res (gram_tc.cu).
+cudaError_t launch_s_prefix(const double *S, int64_t T, int64_t s, int64_t n_res, int64_t pstride,
+                            double *prefix, cudaStream_t st);
 
 // Maps a failed CUDA call to TCORR_ECUDA; with TCORR_VERBOSE set in the
 // environment it also prints the call site and CUDA's error string.
