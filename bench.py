@@ -51,6 +51,9 @@ WORKLOADS = {
     "flux": dict(label="Green-Kubo flux ACF: (Pxy, Pxz, Pyz) as [T][1][3], AR(1) phi=0.999 unit variance, "
                        "T=2,000,000 plus 64 series of T=200,000, tau_max=20,000, ACF + running viscosity "
                        "integral", T=2000000, Tshort=200000, nshort=64, tau_max=20000, phi=0.999),
+    "viscosity": dict(label="viscosity ACF with a long window: (Pxy, Pxz, Pyz) as [T][1][3], AR(1) phi=0.999, "
+                           "T=2,000,000, tau_max=500,000, ACF + running integral; FFT route vs polyphase "
+                           "tensor core", T=2000000, tau_max=500000, phi=0.999),
     "small": dict(N=512, T=1000, tau_max=500, stride=1, sigma=0.01, box=3.0, gamma=0.1, sites=1,
                   dt=1.0, label="small MSD + VACF: N=512, T=1000, tau_max=500, stride 1"),
 }
@@ -179,11 +182,11 @@ def oracle_sample(xh, vh, wl, target_s):
     n_lags = int(max(2, min(tm + 1, target_s / max(t_probe, 1e-3))))
     lags = np.unique(np.linspace(0, tm, n_lags).astype(np.int64))
     t0 = time.perf_counter()
-    oracle.msd(xh, stride=s, lags=lags)
-    oracle.acf(vh, stride=s, lags=lags)
+    m_ref = oracle.msd(xh, stride=s, lags=lags)
+    c_ref = oracle.acf(vh, stride=s, lags=lags)
     el = time.perf_counter() - t0
     n_up = 2 * int(sum(N * ((T - 1 - int(l)) // s + 1) for l in lags))
-    return n_up / el, cores, len(lags), el
+    return n_up / el, cores, len(lags), el, (lags, m_ref, c_ref)
 
 
 def run_reference(args, wl):
@@ -196,10 +199,10 @@ def run_reference(args, wl):
     vh = synth.ou_velocities(wl["T"], wl["N"], wl["gamma"], 1.0, synth.BASE_SEED + 1)
     per_step = float(os.environ.get("TCORR_REF_STEP_S", "3.0"))
     for _ in range(args.warmup):
-        oracle_sample(xh, vh, wl, per_step / 4)
+        oracle_sample(xh, vh, wl, per_step / 4)[:4]
     rates, tot_t, cores, nl = [], 0.0, 1, 0
     for _ in range(args.steps):
-        r, cores, nl, el = oracle_sample(xh, vh, wl, per_step)
+        r, cores, nl, el = oracle_sample(xh, vh, wl, per_step)[:4]
         rates.append(r)
         tot_t += el
     value = float(statistics.median(rates))
@@ -305,6 +308,8 @@ def run_gpu(args, wl):
 
     from paper_1708_08619_gb300 import shard
     ms_per_step = shard.max_over_ranks(elapsed_ms / args.steps)
+    m_dev = out_m.cpu().numpy().copy()       # the timed steps' results (checked against the oracle below)
+    c_dev = out_c.cpu().numpy().copy()
     u_step = updates(N, T, tm, s) * 2
     value = u_step * world / (ms_per_step / 1000.0)
 
@@ -455,13 +460,20 @@ def run_gpu(args, wl):
         del ws_p
 
     cpu = None
+    err_vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         xhn = xh.numpy()
         vhn = vh.numpy()
-        r, cores, nl, el = oracle_sample(xhn, vhn, wl, float(os.environ.get("TCORR_CPU_S", "12")))
+        r, cores, nl, el, (lags, m_ref, c_ref) = oracle_sample(xhn, vhn, wl,
+                                                               float(os.environ.get("TCORR_CPU_S", "12")))
         cpu = {"value": r, "unit": "updates/s", "cores": cores, "kind": "oracle",
                "sample": f"MSD and VACF at {nl} evenly spaced lags in [0, {tm}], all atoms and "
                          f"origins of the same arrays; {el:.1f} s"}
+        # the timed steps' results against the oracle at those lags (the metric's 1e-5 bar)
+        err_vs_oracle = {"lags": int(nl),
+                         "msd_max_abs_over_msd_tau_max": float(np.max(np.abs(m_dev[lags] - m_ref)) / m_ref[-1]),
+                         "acf_max_abs_over_c0": float(np.max(np.abs(c_dev[lags] - c_ref)) / abs(c_ref[0])),
+                         "tolerance": 1e-6 if method == "plain" else 1e-5}
 
     dtype = {"plain": "f32", "fp16x3": "f16x3 (f32 accumulate)", "bf16x3": "bf16x3 (f32 accumulate)",
              "bf16x4": "bf16x4 (f32 accumulate)", "tf32x3": "tf32x3 (f32 accumulate)"}.get(method, method)
@@ -474,7 +486,8 @@ def run_gpu(args, wl):
                        "l2": "inputs larger than L2 (2 x %.2f GB), no flush" % (T * N * 12 / 1e9),
                        "msd_ms": statistics.mean(msd_ms), "acf_ms": statistics.mean(acf_ms),
                        "msd_kernel_ms": msd_avg_s * 1000.0, "acf_kernel_ms": acf_avg_s * 1000.0,
-                       "updates_per_step": u_step, "plain_comparison": plain_cmp},
+                       "updates_per_step": u_step, "plain_comparison": plain_cmp,
+                       "error_vs_oracle": err_vs_oracle},
             "clocks": clocks,
             "e2e": dict({"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h}, **e2e_info),
@@ -682,6 +695,76 @@ def run_flux_workload(args, wl):
         dist.destroy_process_group()
 
 
+def run_viscosity_workload(args, wl):
+    """One long flux series with a correlation window of a quarter of its length
+    (the paper's viscosity case: 2e6 points, window 5e5): the ACF and its running
+    integral by the FFT route and by the polyphase tensor-core form, each checked
+    against the oracle at sampled lags.  (The plain kernel's per-tile partial sums
+    would need about 125 GB of workspace at this window.)"""
+    import torch
+    import oracle
+    from paper_1708_08619_gb300 import build as tbuild
+    from paper_1708_08619_gb300 import synth, tcorr
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tbuild.build()
+    tcorr.load()
+    Tn, tm = wl["T"], wl["tau_max"]
+    xh = synth.ar1_flux(Tn, wl["phi"], seed=synth.BASE_SEED + 7 + 100 * rank)
+    x = torch.from_numpy(xh).to(dev)
+    u = updates(1, Tn, tm, 1)
+    lags = np.unique(np.concatenate([[0, 1, 2, tm], np.linspace(0, tm, 61).astype(np.int64)]))
+    ref = oracle.acf(xh, stride=1, lags=lags) if not args.no_cpu_baseline else None
+    stream = torch.cuda.Stream(dev)
+    res = {}
+    for method in ("fft", "fp16x3"):
+        out = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+        gk = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+        ws = torch.empty(max(256, tcorr.tcorr_workspace_size(Tn, 1, tm, 1, method)), dtype=torch.uint8, device=dev)
+        steps = args.steps if method == "fft" else max(1, min(2, args.steps))
+        with torch.cuda.stream(stream):
+            def step():
+                tcorr.tcorr_acf(x, tm, 1, method, out=out, ws=ws, stream=stream)
+                tcorr.gk_integrate(out, 1.0, 1.0 / 3.0, out=gk, stream=stream)
+            for _ in range(max(3, args.warmup) if method == "fft" else 1):
+                step()
+            stream.synchronize()
+            sampler = ClockSampler(gpu_identifier(torch, local)) if method == "fft" else None
+            if sampler:
+                sampler.start()
+                time.sleep(0.3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            stream.synchronize()
+            clocks = sampler.stop() if sampler else None
+        got = out.cpu().numpy()
+        err = float(np.max(np.abs(got[lags] - ref)) / abs(ref[0])) if ref is not None else None
+        res[method] = {"ms_per_step": e0.elapsed_time(e1) / steps, "err_over_c0": err, "clocks": clocks}
+        del ws
+    ms = res["fft"]["ms_per_step"]
+    line = {"metric": "origin.lag pairs/s of the 3-component flux ACF, long window", "value": u / (ms / 1000.0),
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 transforms (fft)", "data": "synthetic",
+            "config": {"workload": wl["label"], "pairs_per_step": u,
+                       "methods": {m: {"ms_per_step": r["ms_per_step"], "err_vs_oracle_over_c0": r["err_over_c0"]}
+                                   for m, r in res.items()},
+                       "fft_speedup_vs_polyphase_tc": res["fp16x3"]["ms_per_step"] / ms,
+                       "oracle_lags": int(len(lags))},
+            "clocks": res["fft"]["clocks"], "e2e": None,
+            # this library's kernels per FFT step: gather, power spectrum, lag sum, finalize,
+            # Green-Kubo (the two transforms are cuFFT's kernels, not counted)
+            "gpu_launches": 5 * args.steps,
+            "roofline": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,6 +785,8 @@ def main():
         run_batch_workload(args, wl)
     elif args.workload == "flux":
         run_flux_workload(args, wl)
+    elif args.workload == "viscosity":
+        run_viscosity_workload(args, wl)
     else:
         run_gpu(args, wl)
 

@@ -1,5 +1,6 @@
 // C ABI of libtcorr.so (declared in include/tcorr.h): argument validation,
 // work planning, workspace carving and dispatch to the kernels.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -80,13 +81,21 @@ size_t plain_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     return align256(sizeof(double) * static_cast<size_t>(p.n_items) * p.WP);
 }
 
+// AUTO: the FFT route when its cost estimate is below the band form's, else
+// the FP16 x3 tensor-core form (plain without a tensor-core device).  Costs
+// per K column, calibrated on GB300: band about 6.5e-15 s per (origin, lag)
+// pair (T (tau_max + 128) of them), FFT about 1.5e-11 s per L log2 L of the
+// padded transform length; e.g. T = 2e6 switches to the FFT above
+// tau_max ~ 1.3e5, and T <= 1e5 never does.
 int resolve_method(int method, int64_t T, int64_t N, int64_t tau_max, int64_t s) {
-    (void)T;
     (void)N;
-    (void)tau_max;
     (void)s;
     if (method != TCORR_AUTO) return method;
-    return gram_method_available(TCORR_TC_FP16X3) ? TCORR_TC_FP16X3 : TCORR_PLAIN;
+    if (!gram_method_available(TCORR_TC_FP16X3)) return TCORR_PLAIN;
+    const double L = 2.0 * static_cast<double>(T + tau_max);      // padded length, within 2x
+    const double band = 6.5e-15 * static_cast<double>(T) * static_cast<double>(tau_max + 128);
+    const double fft = 1.5e-11 * L * std::log2(L);
+    return fft < band ? TCORR_FFT : TCORR_TC_FP16X3;
 }
 
 }  // namespace
