@@ -69,3 +69,48 @@ def test_two_gloo_ranks_share_a_batch_and_agree_on_the_step_time():
         flat = sorted(i for s in gathered for i in s)
         assert flat == list(range(len(shapes)))
         assert gathered[rank] == mine
+
+
+def test_atom_ranges_cover_the_atoms_once():
+    for N in (1, 7, 64, 1001):
+        for world in (1, 2, 3, 8):
+            rs = [shard.atom_range(N, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == N
+            assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+            sizes = [b - a for a, b in rs]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def _atom_worker(rank, world, port, q):
+    import torch.distributed as dist
+    import oracle
+    from paper_1708_08619_gb300 import synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x = synth.random_walk_positions(120, 37, 0.02, 2.0, seed=91)
+    a0, a1 = shard.atom_range(37, rank, world)
+    # each rank's share: the oracle stands in for the device library on CPU
+    part = torch.from_numpy(oracle.msd(np.ascontiguousarray(x[:, a0:a1]), 60, 2))
+    whole = shard.combine_atom_shards(part, a1 - a0)
+    dist.destroy_process_group()
+    q.put((rank, whole.numpy()))
+
+
+def test_two_gloo_ranks_combine_atom_shards():
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_1708_08619_gb300 import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_atom_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    want = oracle.msd(synth.random_walk_positions(120, 37, 0.02, 2.0, seed=91), 60, 2)
+    for _, got in results:
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
