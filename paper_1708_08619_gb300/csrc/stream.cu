@@ -15,10 +15,11 @@
 //
 // Copies: two window buffers alternate.  Window c's halo (its first tau_max
 // frames) is the tail of window c-1 and is copied device to device; only the
-// C new frames cross from the host, so each frame crosses once.  Copies run
+// new frames cross from the host, so each frame crosses once.  Copies run
 // on a second stream and overlap the previous window's kernels; events order
 // buffer reuse.
 #include <cstdint>
+#include <vector>
 
 #include "tcorr_internal.cuh"
 
@@ -38,17 +39,38 @@ int64_t default_chunk(int64_t tau_max, int64_t s) {
 struct StreamPlan {
     int method;                 // resolved (never TCORR_AUTO)
     int64_t K, C, W, n_win;     // K = 3N; origins per window; largest window; windows
+    std::vector<int64_t> start; // first frame of each window (multiples of s), then T
     size_t off_buf[2], off_engine, engine_bytes, total;
 };
 
+// Windows of C origin frames, except that the last stretch is cut so that the
+// final window holds at most a quarter of C: its kernels are the part of the
+// call that no copy overlaps.
+std::vector<int64_t> window_starts(int64_t T, int64_t C, int64_t s) {
+    std::vector<int64_t> st;
+    int64_t q = (C / 4 / s) * s;
+    if (q < s) q = s;
+    int64_t t = 0;
+    while (t < T) {
+        st.push_back(t);
+        const int64_t rem = T - t;
+        if (rem > C + q) t += C;
+        else if (rem > q) t += ceil_div(rem - q, s) * s;
+        else t = T;
+    }
+    st.push_back(T);
+    return st;
+}
+
+// Frames held by window c: its origin frames plus the tau_max halo.
 int64_t window_frames(const StreamPlan &P, int64_t T, int64_t tau_max, int64_t c) {
-    const int64_t t0 = c * P.C, w = P.C + tau_max;
+    const int64_t t0 = P.start[c], w = (P.start[c + 1] - t0) + tau_max;
     return T - t0 < w ? T - t0 : w;
 }
 
-Window window_of(const StreamPlan &P, int64_t Wc, int64_t s) {
-    const int64_t first = P.C < Wc ? P.C : Wc;          // frames whose origins start pairs here
-    return Window{(first - 1) / s + 1, true};
+Window window_of(const StreamPlan &P, int64_t c, int64_t s) {
+    const int64_t len = P.start[c + 1] - P.start[c];     // frames whose origins start pairs here
+    return Window{(len - 1) / s + 1, true};
 }
 
 bool make_stream_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int64_t chunk,
@@ -63,9 +85,10 @@ bool make_stream_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int meth
     if (C > Tcap) C = Tcap;
     P->C = C;
     P->W = T < C + tau_max ? T : C + tau_max;
-    P->n_win = ceil_div(T, C);
+    P->start = window_starts(T, C, s);
+    P->n_win = static_cast<int64_t>(P->start.size()) - 1;
     const int64_t tm = tau_max < P->W - 1 ? tau_max : P->W - 1;
-    const Window w = window_of(*P, P->W, s);
+    const Window w{(C < T ? C - 1 : T - 1) / s + 1, true};    // the largest window's origins
     P->engine_bytes = P->method == TCORR_PLAIN ? plain_window_workspace(P->W, N, tm, s, w.orig_cap)
                                                : gram_workspace_size(P->W, N, tm, s, P->method, &w);
     if (P->engine_bytes == 0 && P->method != TCORR_PLAIN) return false;
@@ -121,14 +144,15 @@ int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max
         return cuda_fail(e, "stream fork");
     for (int64_t c = 0; c < P.n_win; ++c) {
         const int b = static_cast<int>(c & 1);
-        const int64_t t0 = c * P.C, Wc = window_frames(P, T, tau_max, c);
+        const int64_t t0 = P.start[c], Wc = window_frames(P, T, tau_max, c);
         if (c >= 2 && (e = cudaStreamWaitEvent(R.side, R.freed[b], 0)) != cudaSuccess)
             return cuda_fail(e, "buffer reuse wait");
         int64_t have = 0;
-        if (c > 0) {        // halo: frames [t0, t0 + h) sit at frame C of the previous window
+        if (c > 0) {        // halo: frames [t0, t0 + h) follow the previous window's origin frames
             have = tau_max < Wc ? tau_max : Wc;
+            const int64_t prev_len = t0 - P.start[c - 1];
             if (have > 0 &&
-                (e = cudaMemcpyAsync(buf[b], buf[1 - b] + static_cast<size_t>(P.C) * P.K, have * row,
+                (e = cudaMemcpyAsync(buf[b], buf[1 - b] + static_cast<size_t>(prev_len) * P.K, have * row,
                                      cudaMemcpyDeviceToDevice, R.side)) != cudaSuccess)
                 return cuda_fail(e, "halo copy");
         }
@@ -140,7 +164,7 @@ int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max
             (e = cudaStreamWaitEvent(st, R.copied[b], 0)) != cudaSuccess)
             return cuda_fail(e, "window copy event");
         const int64_t tm = tau_max < Wc - 1 ? tau_max : Wc - 1;
-        const Window w = window_of(P, Wc, s);
+        const Window w = window_of(P, c, s);
         const int rc = P.method == TCORR_PLAIN
                            ? plain_run(kind, buf[b], Wc, N, tm, s, d_out, ws + P.off_engine, P.engine_bytes, st, &w)
                            : gram_run(kind, buf[b], Wc, N, tm, s, P.method, d_out, ws + P.off_engine,
