@@ -143,8 +143,9 @@ int tcorr_acf(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s
  *   of two species (or weighted by charge) it gives the collective
  *   cross-correlations of Green-Kubo transport (interdiffusion, charge
  *   current).  The paper computes autocorrelations only; this is the same loop
- *   nest with two signals.  Both methods use the band form for every K (the
- *   small-K polyphase form of tcorr_acf is not used here).
+ *   nest with two signals.  Small K (3N <= 24, stride 1, tau_max >= 383) uses
+ *   the polyphase form as tcorr_acf does, with the unshifted operand copy of A
+ *   on the origin side and the shifted copies of B on the other.
  * d_a, d_b: [T][N][3] float32, 4-byte aligned; d_out: tau_max+1 doubles,
  * 8-byte aligned; d_ws: tcorr_xcf_workspace_size(...) bytes (the tensor-core
  * methods keep split copies of both signals), 256-byte aligned.

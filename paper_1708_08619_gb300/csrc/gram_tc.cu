@@ -1067,6 +1067,7 @@ struct PolyPrepArgs {
     float *inv_scale;                // [L]
     unsigned *rowmax;                // [L] FP16: bits of the largest |value| per phase row (zeroed first)
     int kind;
+    int ncopies;                     // shifted copies written: 8, or 1 for the origin side of a cross-correlation
     int64_t rm_begin, tile_begin;    // batch: first row-max block / prep tile of this instance
 };
 
@@ -1169,8 +1170,8 @@ __device__ __forceinline__ void poly_split_body(const PolyPrepArgs &a, int64_t t
         if (two) V[row * PT_LD + tid + PREP_THREADS] = v1;
     }
     __syncthreads();
-    constexpr int UNITS = 8 * POLY_L * (PT_K / 8);   // (copy r, phase j, octet) -> 8 elements
-    for (int u = tid; u < UNITS; u += PREP_THREADS) {
+    const int units = a.ncopies * POLY_L * (PT_K / 8);   // (copy r, phase j, octet) -> 8 elements
+    for (int u = tid; u < units; u += PREP_THREADS) {
         const int oct = u & (PT_K / 8 - 1);
         const int rj = u / (PT_K / 8);
         const int r = rj / POLY_L, j = rj - r * POLY_L;
@@ -1247,7 +1248,7 @@ __device__ __forceinline__ void poly_reduce_body(const PolyReduceArgs &a, int64_
     const int64_t no = a.T - tau;
     const double denom = static_cast<double>(a.N) * static_cast<double>(no);
     double v;
-    if (a.kind == 1) {
+    if (a.kind != 0) {             // autocorrelation or cross-correlation
         v = sum / denom;
     } else if (tau == 0) {
         v = 0.0;
@@ -1351,9 +1352,16 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
         return o;
     };
     const size_t copies = size_t(8) * POLY_L * L->Kalloc * L->esize;
-    L->off_xh = take(copies);
-    L->off_xl = take(copies);
+    L->cross = kind == 2;
+    // a cross-correlation reads only the unshifted copy of its origin-side signal A
+    L->off_xh = take(L->cross ? copies / 8 : copies);
+    L->off_xl = take(L->cross ? copies / 8 : copies);
     L->off_scale = take(size_t(2 * POLY_L) * sizeof(float));      // inv_scale, then row maxima
+    if (L->cross) {
+        L->off_bh = take(copies);
+        L->off_bl = take(copies);
+        L->off_scale_b = take(size_t(2 * POLY_L) * sizeof(float));
+    }
     L->off_S = take(kind == 0 ? size_t(T) * sizeof(double) : 0);
     L->off_prefix = take(kind == 0 ? size_t(T + 1) * sizeof(double) : 0);
     L->off_partial = take(size_t(L->p.n_items) * WPG * sizeof(double));
@@ -1371,7 +1379,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->bke = L->prec == P_TF32 ? 16 : 32;
     const int64_t K = 3 * N;
     L->cross = kind == 2;
-    L->poly = !w && !L->cross && use_polyphase(T, N, tau_max, s);
+    L->poly = !w && use_polyphase(T, N, tau_max, s);
     if (L->poly) return make_poly_layout(T, N, tau_max, method, kind, L);
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
@@ -1646,11 +1654,13 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
 // kernel's tensor maps and arguments, and the reduction arguments.
 struct PolySetup {
     PolyPrepArgs prep;
+    PolyPrepArgs prep_b;            // cross-correlation: the later-side signal B
     InstDesc gram;
     PolyReduceArgs red;
 };
 
-int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, PolySetup *P) {
+int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, PolySetup *P,
+               const float *d_y = nullptr) {
     const int64_t T = L.p.T, N = L.p.N;
     PolyPrepArgs &pa = P->prep;
     pa.X = d_x;
@@ -1664,9 +1674,20 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     pa.Yl = base + L.off_xl;
     pa.inv_scale = reinterpret_cast<float *>(base + L.off_scale);
     pa.rowmax = reinterpret_cast<unsigned *>(base + L.off_scale) + POLY_L;
-    pa.kind = kind;
+    pa.kind = L.cross ? 1 : kind;
+    pa.ncopies = L.cross ? 1 : 8;
     pa.rm_begin = 0;
     pa.tile_begin = 0;
+    if (L.cross) {
+        PolyPrepArgs &pb = P->prep_b;
+        pb = pa;
+        pb.X = d_y;
+        pb.Yh = base + L.off_bh;
+        pb.Yl = base + L.off_bl;
+        pb.inv_scale = reinterpret_cast<float *>(base + L.off_scale_b);
+        pb.rowmax = reinterpret_cast<unsigned *>(base + L.off_scale_b) + POLY_L;
+        pb.ncopies = 8;
+    }
     EncodeFn encode = get_encode();
     if (!encode) return TCORR_EUNSUPPORTED;
     const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -1674,6 +1695,7 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     CUtensorMap *maps = P->gram.maps;
     void *bases[2] = {base + L.off_xh, base + L.off_xl};
+    void *bbases[2] = {base + (L.cross ? L.off_bh : L.off_xh), base + (L.cross ? L.off_bl : L.off_xl)};
     const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kalloc * L.esize);
     for (int h = 0; h < 2; ++h) {
         const cuuint64_t dimA[2] = {static_cast<cuuint64_t>(L.Kalloc), POLY_L};
@@ -1690,7 +1712,7 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
         for (int v = 0; v < 2; ++v) {          // B with BF-row boxes, then with NBOX-row boxes
             const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(v == 0 ? BF : NBOX),
                                         1};
-            if (encode(&maps[2 + 2 * v + h], dt, 3, bases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            if (encode(&maps[2 + 2 * v + h], dt, 3, bbases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase B)");
@@ -1709,7 +1731,7 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     ga.kb_total = ceil_div(L.Kprime, L.bke);
     ga.kb_per_item = L.kseg / L.bke;
     ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
-    ga.inv_scale_b = ga.inv_scale;
+    ga.inv_scale_b = L.cross ? reinterpret_cast<const float *>(base + L.off_scale_b) : ga.inv_scale;
     ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = 2;
     ga.sub_kb = L.sub_kb;
@@ -1764,30 +1786,33 @@ cudaError_t poly_msd_s(const float *d_x, const GramLayout &L, uint8_t *base, cud
 // Enqueues one polyphase instance: operand copies, S(t) and its prefix sums
 // (MSD), the Gram kernel over (q, h, c) blocks, and the lag reduction.
 int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, double *d_out, int num_sms,
-             cudaStream_t st) {
+             cudaStream_t st, const float *d_y = nullptr) {
     PolySetup P;
-    int rc = poly_setup(kind, d_x, L, base, d_out, &P);
+    int rc = poly_setup(kind, d_x, L, base, d_out, &P, d_y);
     if (rc != TCORR_OK) return rc;
     cudaError_t e = cudaSuccess;
-    if (L.prec == P_FP16) {
-        if ((e = cudaMemsetAsync(P.prep.rowmax, 0, POLY_L * sizeof(unsigned), st)) != cudaSuccess)
-            return cuda_fail(e, "row-max reset");
-        poly_rowmax_kernel<<<static_cast<unsigned>(poly_rm_blocks(L.P)), POLY_L, 0, st>>>(P.prep);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_rowmax_kernel launch");
+    for (int side = 0; side < (L.cross ? 2 : 1); ++side) {      // the signal, then B of a cross-correlation
+        const PolyPrepArgs &pp = side == 0 ? P.prep : P.prep_b;
+        if (L.prec == P_FP16) {
+            if ((e = cudaMemsetAsync(pp.rowmax, 0, POLY_L * sizeof(unsigned), st)) != cudaSuccess)
+                return cuda_fail(e, "row-max reset");
+            poly_rowmax_kernel<<<static_cast<unsigned>(poly_rm_blocks(L.P)), POLY_L, 0, st>>>(pp);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poly_rowmax_kernel launch");
+        }
+        if ((e = poly_split_launch(L.prec, false, &pp, 1, static_cast<unsigned>(poly_tiles(L.Kalloc)), st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "poly_split_kernel launch");
     }
-    if ((e = poly_split_launch(L.prec, false, &P.prep, 1, static_cast<unsigned>(poly_tiles(L.Kalloc)), st)) !=
-        cudaSuccess)
-        return cuda_fail(e, "poly_split_kernel launch");
     if (kind == 0 && (e = poly_msd_s(d_x, L, base, st)) != cudaSuccess) return cuda_fail(e, "poly S launch");
     const GramArgs &ga = P.gram.ga;
     if ((e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
         return cuda_fail(e, "work-item counter reset");
     const int grid = static_cast<int>(ga.n_items < num_sms ? ga.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
-        case P_FP16 * 2: e = launch_gram<P_FP16, false>(P.gram.maps, ga, grid, st, kind); break;
-        case P_BF16 * 2: e = launch_gram<P_BF16, false>(P.gram.maps, ga, grid, st, kind); break;
-        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(P.gram.maps, ga, grid, st, kind); break;
-        default: e = launch_gram<P_TF32, false>(P.gram.maps, ga, grid, st, kind); break;
+        case P_FP16 * 2: e = launch_gram<P_FP16, false>(P.gram.maps, ga, grid, st, kind & 1); break;
+        case P_BF16 * 2: e = launch_gram<P_BF16, false>(P.gram.maps, ga, grid, st, kind & 1); break;
+        case P_BF16 * 2 + 1: e = launch_gram<P_BF16, true>(P.gram.maps, ga, grid, st, kind & 1); break;
+        default: e = launch_gram<P_TF32, false>(P.gram.maps, ga, grid, st, kind & 1); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "gram_band_kernel (polyphase) launch");
     poly_reduce_kernel<<<static_cast<unsigned>(ceil_div(L.p.tau_max + 1, 256)), 256, 0, st>>>(P.red);
@@ -1846,7 +1871,7 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     int num_sms = 0;
     if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
-    if (L.poly) return poly_run(kind, d_x, L, ws, d_out, num_sms, st);
+    if (L.poly) return poly_run(kind, d_x, L, ws, d_out, num_sms, st, d_y);
 
     auto split = [&](const SplitDesc &q) {
         switch (L.prec) {

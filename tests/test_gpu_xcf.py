@@ -63,3 +63,17 @@ def test_xcf_order_of_the_signals_matters(T):
     assert int(np.argmax(ab)) == 0 and abs(int(np.argmax(ba)) - 25) <= 3
     ref_ba = oracle.xcf(b, a, 100)
     assert np.max(np.abs(ba - ref_ba)) / scale_of(a, b) <= parity.TC_TOL
+
+
+@pytest.mark.parametrize("method", ["fp16x3", "tf32x3"])
+@pytest.mark.parametrize("N,Tn,tm", [(1, 6000, 1500), (8, 3000, 700)])
+def test_xcf_small_k_polyphase(T, method, N, Tn, tm):
+    """K = 3N <= 24, stride 1, tau_max >= 383: the polyphase form, with the
+    unshifted copy of A on the origin side and 8 shifted copies of B."""
+    a, b = pair(Tn, N, synth.BASE_SEED + 7 * N, lag=40)
+    got = T.tcorr_xcf(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), tm, 1, method).cpu().numpy()
+    ref = oracle.xcf(a, b, tm, 1)
+    assert np.max(np.abs(got - ref)) / scale_of(a, b) <= parity.TC_TOL
+    x = torch.from_numpy(a).cuda()
+    # X(A, A) on the polyphase form equals the polyphase autocorrelation bit for bit
+    assert np.array_equal(T.tcorr_xcf(x, x, tm, 1, method).cpu().numpy(), T.tcorr_acf(x, tm, 1, method).cpu().numpy())
