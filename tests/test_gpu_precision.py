@@ -43,7 +43,7 @@ def data(T):
     return x, v, rm, rc
 
 
-@pytest.mark.parametrize("method", ["fp16x3", "tf32x3", "bf16x4"])
+@pytest.mark.parametrize("method", ["fp16x3", "tf32x3", "bf16x4", "bf16x3"])
 def test_precision_workload(T, data, method):
     x, v, rm, rc = data
     ws = torch.empty(T.tcorr_workspace_size(TN, NA, TM, 1, method), dtype=torch.uint8, device="cuda")
