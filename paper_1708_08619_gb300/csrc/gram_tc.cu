@@ -70,7 +70,14 @@ constexpr int WPG = 320;            // window width per item (>= BO + BF - 1 = 3
 constexpr int NTHREADS = 320;   // 10 warps
 constexpr int NEPI = 8;          // epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int kSubKb = 3;           // K-blocks per TMEM accumulation sub-chain (default)
+// K-blocks per TMEM accumulation sub-chain (defaults).  The tensor core's FP32
+// accumulation drifts low by about the same amount per accumulate step, so the
+// error grows linearly with the chain (water-scale MSD: 2.6 / 3.5 / 5.5 e-6 of
+// MSD(tau_max) at 3 / 4 / 6 K-blocks) while longer chains hand fewer partial
+// sums to the epilogue (18.66 / 17.94 / 17.40 ms per step).  Band form: 4;
+// polyphase (flux ACF 1.3e-6 of C(0) at 6, 9.5% faster than at 3): 6.
+constexpr int kSubKb = 4;
+constexpr int kSubKbPoly = 6;
 
 // Manual overrides: TCORR_KSEG (K elements per work item, a multiple of 64)
 // and TCORR_SUB_KB (K-blocks per accumulation sub-chain, 1..8).  Longer
@@ -1321,7 +1328,7 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
     if (L->Kalloc >= (int64_t(1) << 31)) return false;
     const int64_t kb_total = ceil_div(L->Kprime, L->bke);
     {
-        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq), kSubKb};
+        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq), kSubKbPoly};
         if (const TuneChoice *o = get_tune_override()) c = *o;
         if (const int64_t ek = env_kseg()) c.kseg = ek;
         if (const int es = env_sub_kb()) c.sub_kb = es;
