@@ -157,3 +157,31 @@ def test_stream_workspace_holds_two_windows(lib):
     # a chunk covering the whole trajectory is one window of T frames
     assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 10 ** 9) >= 2 * T * N * 3 * 4
     assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, -1) == 0
+
+
+def call_xcf(lib, a=FAKE_X, b=FAKE_X + 0x1000, T=100, N=10, tau_max=50, s=1, method=0, out=FAKE_OUT,
+             ws=FAKE_WS, ws_bytes=0):
+    return lib.tcorr_xcf(a, b, T, N, tau_max, s, method, out, ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(a=None), dict(b=None), dict(out=None), dict(T=0), dict(N=0), dict(tau_max=100), dict(s=0),
+    dict(method=99),
+])
+def test_xcf_invalid_arguments(lib, kw):
+    assert call_xcf(lib, **kw) == 1
+
+
+def test_xcf_misaligned_and_workspace(lib):
+    assert call_xcf(lib, a=FAKE_X + 2) == 2
+    assert call_xcf(lib, b=FAKE_X + 0x1000 + 1) == 2
+    assert call_xcf(lib, out=FAKE_OUT + 4) == 2
+    need = lib.tcorr_xcf_workspace_size(100, 10, 50, 1, 0)
+    assert need > 0
+    assert call_xcf(lib, ws_bytes=need - 1) == 4
+
+
+def test_fft_method_is_known():
+    """Method 6 (FFT route) passes argument validation; its workspace size
+    comes from cuFFT plans and is 0 without a device."""
+    assert tcorr.METHODS["fft"] == 6
