@@ -13,31 +13,38 @@
 // Split precision: each FP32 value is written as x = hi + lo with hi and lo in
 // a 16-bit (or TF32) format and G is accumulated from hi.hi + hi.lo + lo.hi
 // (x3; x4 adds lo.lo) in FP32 in tensor memory.  FP16 operands carry a
-// per-frame power-of-two scale (so |x| <= 2^14 and hi, lo stay normal);
-// BF16 and TF32 need none.  S(t) is formed from the FP32 values in FP64.
+// power-of-two scale per (frame, K-group) (so |x| <= 2^14 and hi, lo stay
+// normal; a K-group is the K range one work item contracts); BF16 and TF32
+// need none.  S(t) is formed from the FP32 values in FP64.
 //
 // Kernels, in launch order:
-//   split_kernel      one block per frame: reference, scale, split, S(t)
+//   split_kernel      one block per (frame, K-group): reference, scale,
+//                     split, the group's part of S(t)
+//   s_combine_kernel  S(t) = sum of the group parts (MSD only)
 //   s_prefix_kernel   per-residue FP64 prefix sums of S (MSD only)
 //   gram_band_kernel  persistent, warp-specialised band tiles (below)
 //   lag_reduce        (reduce.cu) fixed-order FP64 reduction + MSD assembly
+// A cross-correlation splits its two signals separately (B into its own
+// copies) and skips S; small K uses the polyphase form further down.
 //
 // gram_band_kernel: one CTA per SM, 10 warps.
-//   warp 0     TMA producer: per K-block loads A_hi, A_lo (128 origin rows)
-//              and B_hi, B_lo (192 frame rows) into a 5-stage smem ring
+//   warp 0     TMA producer: claims work items from a global counter and,
+//              per K-block, loads A_hi, A_lo (128 origin rows) and B_hi,
+//              B_lo (192 frame rows; the narrow last column tile of a band
+//              row only the 32-row boxes it needs) into a 5-stage smem ring
 //              (64-byte rows, 64B swizzle).
 //   warp 1     allocates TMEM (two 128 x 192 FP32 accumulators)
 //              and, from one lane, issues the tcgen05.mma chain.  The chain
-//              of a work item is cut into short sub-chains (sub_kb K-blocks,
-//              12 MMAs for x3) that alternate between the two accumulators:
-//              the tensor core's FP32 accumulation loses low bits on every
-//              accumulate step, so a long chain drifts low; short chains keep
-//              that loss small.
+//              of a work item is cut into sub-chains (sub_kb K-blocks of 6
+//              MMAs each for x3) that alternate between the two
+//              accumulators: the tensor core's FP32 accumulation loses low
+//              bits on every accumulate step, so a long chain drifts low;
+//              short chains keep that loss small.
 //   warps 2-9  epilogue: two warps per TMEM lane quadrant, 96 columns each.
 //              Each sub-chain's accumulator is read with tcgen05.ld and added
 //              (FP32, round to nearest) into a per-thread register copy of
-//              its 128 entries; at the end of the item the band mask, the
-//              per-frame unscale and the diagonal sums (band offset
+//              its 96 entries; at the end of the item the band mask, the
+//              per-(frame, group) unscale and the diagonal sums (band offset
 //              w = j - i + 127) go to per-warp shared buffers, and a
 //              fixed-order combine writes one FP64 window per work item.
 #include <cuda.h>
@@ -280,8 +287,9 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 // One work item, decoded.  A rows start at a_y, B rows at (b_x, b_y, b_z)
 // (b_x: extra K offset; b_z: shifted operand copy, polyphase only).  Entry
 // (row i, column j) of the tile holds band offset / lag m = moff + j - i,
-// kept if 0 <= m <= m_max.  The per-row FP16 scale of row i is
-// inv_scale[sa0 + i*sstr] and of column j inv_scale[sb0 + j*sstr].  Only
+// kept if 0 <= m <= m_max.  Within the item's K-group g, the FP16 scale of
+// row i is inv_scale[g][sa0 + i*sstr] and of column j
+// inv_scale_b[g][sb0 + j*sstr] (one row per group; polyphase: per phase).  Only
 // columns j < ncol can hold a kept lag (m_max - moff + BO of them, rounded
 // up to the MMA's N granularity of 16): the last column tile of a band row
 // is issued that narrow.
