@@ -87,11 +87,23 @@ bool make_stream_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int meth
     P->W = T < C + tau_max ? T : C + tau_max;
     P->start = window_starts(T, C, s);
     P->n_win = static_cast<int64_t>(P->start.size()) - 1;
-    const int64_t tm = tau_max < P->W - 1 ? tau_max : P->W - 1;
-    const Window w{(C < T ? C - 1 : T - 1) / s + 1, true};    // the largest window's origins
-    P->engine_bytes = P->method == TCORR_PLAIN ? plain_window_workspace(P->W, N, tm, s, w.orig_cap)
-                                               : gram_workspace_size(P->W, N, tm, s, P->method, &w);
-    if (P->engine_bytes == 0 && P->method != TCORR_PLAIN) return false;
+    // Engine workspace: the largest over the windows.  A smaller window can
+    // need more (its plan splits K into more groups to fill the GPU), so every
+    // distinct window shape is sized; full windows all share one shape.
+    P->engine_bytes = 0;
+    bool full_seen = false;
+    for (int64_t c = 0; c < P->n_win; ++c) {
+        const int64_t len = P->start[c + 1] - P->start[c], Wc = window_frames(*P, T, tau_max, c);
+        const bool full = len == C && Wc == C + tau_max;
+        if (full && full_seen) continue;
+        full_seen = full_seen || full;
+        const int64_t tm = tau_max < Wc - 1 ? tau_max : Wc - 1;
+        const Window w = window_of(*P, c, s);
+        const size_t need = P->method == TCORR_PLAIN ? plain_window_workspace(Wc, N, tm, s, w.orig_cap)
+                                                     : gram_workspace_size(Wc, N, tm, s, P->method, &w);
+        if (need == 0 && P->method != TCORR_PLAIN) return false;
+        if (need > P->engine_bytes) P->engine_bytes = need;
+    }
     const size_t buf = align256(static_cast<size_t>(P->W) * static_cast<size_t>(P->K) * sizeof(float));
     P->off_buf[0] = 0;
     P->off_buf[1] = buf;

@@ -127,3 +127,17 @@ def test_stream_repeated_calls_share_a_workspace(T):
         ref = oracle.acf(x, stride=1, lags=np.arange(401))
         check_vs_oracle(1, o.cpu().numpy(), ref, "fp16x3")
     assert T.tcorr_status_poll() == 0
+
+
+@pytest.mark.parametrize("method", ["plain", "fp16x3"])
+def test_stream_small_last_window_large_k(T, method):
+    """N = 8192 (K = 24576), T = 5000, tau_max = 1000, 2048-origin windows: the
+    last window holds 512 origins, and its plan splits K into more groups
+    than a full window's, so it needs more workspace than the largest window
+    (the workspace is the largest over every window shape)."""
+    Tn, N, tm = 5000, 8192, 1000
+    xh = traj(0, Tn, N, 61)
+    got = streamed(T, 0, xh, tm, 1, method, 2048)
+    lags = np.array([0, 1, 2, 127, 128, 500, 999, 1000])
+    ref = oracle.msd(xh, stride=1, lags=lags)
+    check_vs_oracle(0, got[lags], ref, method)
