@@ -93,51 +93,34 @@ __global__ void write_bytes_kernel(uint8_t *dst, const __grid_constant__ ByteChu
 
 // Running trapezoid, I(k) = I(k-1) + dt (c[k-1] + c[k]) / 2, spread over
 // blocks of GK_SPAN increments (FP64 throughput per SM is low on this part,
-// so one block would be slow).  Block b first sums the values before its
-// span, sum_{k<k0} c[k], strided over its threads in a fixed order, which
-// gives the integral up to its start as dt (2 S - c[0] - c[k0-1]) / 2; then
-// each thread integrates GK_PER increments and a fixed warp-shuffle scan
-// combines them.  Deterministic for a given n.
+// so one block would be slow).  Each block integrates its span (GK_PER
+// increments per thread combined by a warp-shuffle scan) on top of the
+// integral up to the span, which comes, in a fixed order, from:
+//   up to GK_RESUM_BLOCKS blocks: one launch; block b sums the values before
+//     its span strided over its threads, S = sum_{k<k0} c[k], and the
+//     integral there is dt (2 S - c[0] - c[k0-1]) / 2;
+//   more blocks (the re-summing would grow as n^2 / GK_SPAN): three
+//     launches; each block sums its span's increments into the first output
+//     slot of its span, one block scans those totals in place (exclusive),
+//     and each block reads its own slot before it writes its span (only
+//     block b writes that slot, so nothing is read after being overwritten).
+// Deterministic for a given n.
 constexpr int GK_THREADS = 256;
 constexpr int GK_PER = 8;
 constexpr int64_t GK_SPAN = int64_t(GK_THREADS) * GK_PER;
+constexpr int GK_SCAN_THREADS = 1024;
+constexpr int64_t GK_RESUM_BLOCKS = 32;
 
-__device__ __forceinline__ double block_allsum(double v, double *sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-#pragma unroll
-    for (int i = 0; i < GK_THREADS / 32; ++i) r += sh[i];
-    __syncthreads();
-    return r;
+__device__ __forceinline__ double gk_inc(const double *c, int64_t k, int64_t n, double dt) {
+    return k < n ? dt * (c[k - 1] + c[k]) / 2.0 : 0.0;
 }
 
-__global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *c, int64_t n, double dt,
-                                                                   double prefactor, double *running) {
-    __shared__ double sh[GK_THREADS / 32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int64_t k0 = 1 + static_cast<int64_t>(blockIdx.x) * GK_SPAN;    // first increment of the span
-    double before = 0.0;
-    if (k0 > 1) {
-        double S = 0.0;
-        for (int64_t k = t; k < k0; k += GK_THREADS) S += c[k];
-        S = block_allsum(S, sh);
-        before = dt * (2.0 * S - c[0] - c[k0 - 1]) / 2.0;
-    }
-    const int64_t kb = k0 + static_cast<int64_t>(t) * GK_PER;
-    double loc[GK_PER];
-    double mine = 0.0;
-#pragma unroll
-    for (int i = 0; i < GK_PER; ++i) {
-        const int64_t k = kb + i;
-        loc[i] = k < n ? dt * (c[k - 1] + c[k]) / 2.0 : 0.0;
-        mine += loc[i];
-    }
-    // exclusive scan of the per-thread sums
-    double inc = mine;
+// Exclusive block scan of one value per thread (fixed shuffle tree); also
+// returns the block total in *total.
+template <int NT>
+__device__ __forceinline__ double block_excl_scan(double v, double *sh, double *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double inc = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const double u = __shfl_up_sync(0xffffffffu, inc, off);
@@ -145,10 +128,76 @@ __global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *
     }
     if (lane == 31) sh[w] = inc;
     __syncthreads();
-    double wbase = 0.0;
-    for (int i = 0; i < w; ++i) wbase += sh[i];
-    double I = before + wbase + (inc - mine);
-    if (blockIdx.x == 0 && t == 0) running[0] = 0.0;
+    double base = 0.0, tot = 0.0;
+    for (int i = 0; i < NT / 32; ++i) {
+        if (i < w) base += sh[i];
+        tot += sh[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return base + (inc - v);
+}
+
+__global__ void __launch_bounds__(GK_THREADS) gk_block_total_kernel(const double *c, int64_t n, double dt,
+                                                                     double *running) {
+    __shared__ double sh[GK_THREADS / 32];
+    const int64_t k0 = 1 + static_cast<int64_t>(blockIdx.x) * GK_SPAN;
+    const int64_t kb = k0 + static_cast<int64_t>(threadIdx.x) * GK_PER;
+    double mine = 0.0;
+#pragma unroll
+    for (int i = 0; i < GK_PER; ++i) mine += gk_inc(c, kb + i, n, dt);
+    double tot;
+    block_excl_scan<GK_THREADS>(mine, sh, &tot);
+    if (threadIdx.x == 0) running[k0] = tot;
+}
+
+// In place: running[1 + b SPAN] <- sum of the totals of blocks before b.
+__global__ void __launch_bounds__(GK_SCAN_THREADS) gk_scan_totals_kernel(double *running, int64_t nb) {
+    __shared__ double sh[GK_SCAN_THREADS / 32];
+    const int64_t per = ceil_div(nb, GK_SCAN_THREADS);
+    const int64_t b0 = static_cast<int64_t>(threadIdx.x) * per, b1 = min(nb, b0 + per);
+    double mine = 0.0;
+    for (int64_t b = b0; b < b1; ++b) mine += running[1 + b * GK_SPAN];
+    double tot;
+    double run = block_excl_scan<GK_SCAN_THREADS>(mine, sh, &tot);
+    for (int64_t b = b0; b < b1; ++b) {
+        const double t = running[1 + b * GK_SPAN];
+        running[1 + b * GK_SPAN] = run;
+        run += t;
+    }
+}
+
+// from_slot: the integral up to this span is the scanned slot; otherwise the
+// block re-sums the values before its span (0 for the first block).
+__global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *c, int64_t n, double dt,
+                                                                   double prefactor, double *running,
+                                                                   int from_slot) {
+    __shared__ double sh[GK_THREADS / 32];
+    __shared__ double before_sh;
+    const int64_t k0 = 1 + static_cast<int64_t>(blockIdx.x) * GK_SPAN;
+    double before = 0.0;
+    if (from_slot) {
+        if (threadIdx.x == 0) before_sh = running[k0];
+        __syncthreads();                    // the slot is read before this block writes its span
+        before = before_sh;
+    } else if (k0 > 1) {
+        double S = 0.0;
+        for (int64_t k = threadIdx.x; k < k0; k += GK_THREADS) S += c[k];
+        double tot;
+        block_excl_scan<GK_THREADS>(S, sh, &tot);
+        before = dt * (2.0 * tot - c[0] - c[k0 - 1]) / 2.0;
+    }
+    const int64_t kb = k0 + static_cast<int64_t>(threadIdx.x) * GK_PER;
+    double loc[GK_PER];
+    double mine = 0.0;
+#pragma unroll
+    for (int i = 0; i < GK_PER; ++i) {
+        loc[i] = gk_inc(c, kb + i, n, dt);
+        mine += loc[i];
+    }
+    double tot;
+    double I = before + block_excl_scan<GK_THREADS>(mine, sh, &tot);
+    if (blockIdx.x == 0 && threadIdx.x == 0) running[0] = 0.0;
 #pragma unroll
     for (int i = 0; i < GK_PER; ++i) {
         const int64_t k = kb + i;
@@ -284,7 +333,13 @@ cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double 
                                 double *d_running, cudaStream_t st) {
     const int64_t blocks = n > 1 ? ceil_div(n - 1, GK_SPAN) : 1;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    gk_integrate_kernel<<<static_cast<unsigned>(blocks), GK_THREADS, 0, st>>>(d_c, n, dt, prefactor, d_running);
+    const unsigned g = static_cast<unsigned>(blocks);
+    const bool three_pass = blocks > GK_RESUM_BLOCKS;
+    if (three_pass) {
+        gk_block_total_kernel<<<g, GK_THREADS, 0, st>>>(d_c, n, dt, d_running);
+        gk_scan_totals_kernel<<<1, GK_SCAN_THREADS, 0, st>>>(d_running, blocks);
+    }
+    gk_integrate_kernel<<<g, GK_THREADS, 0, st>>>(d_c, n, dt, prefactor, d_running, three_pass ? 1 : 0);
     return cudaGetLastError();
 }
 

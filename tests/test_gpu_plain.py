@@ -83,7 +83,8 @@ def test_deterministic_and_workspace_independent(T):
 
 def test_gk_integrate_and_einstein(T):
     rng = np.random.default_rng(9)
-    for n in (1, 2, 3, 1000, 2048, 2049, 2050, 4098, 5001, 20001, 300001):   # block spans of 2048 increments
+    # block spans of 2048 increments; up to 32 blocks one launch, more three
+    for n in (1, 2, 3, 1000, 2048, 2049, 2050, 4098, 5001, 20001, 65537, 65538, 300001):
         cvals = rng.normal(size=n)
         got = T.gk_integrate(dev(cvals), 0.25, 3.5).cpu().numpy()
         want = oracle.gk_integrate(cvals, 0.25, 3.5)
