@@ -170,6 +170,26 @@ __global__ void fft_gather_kernel(const float *__restrict__ x, int64_t T, int64_
     }
 }
 
+// The same for a handful of columns (Kc <= 8, e.g. a flux series with K = 3):
+// one thread per frame reads its Kc values and writes one to each row, so no
+// tile lanes sit idle.
+constexpr int64_t kNarrowGather = 8;
+__global__ void fft_gather_narrow_kernel(const float *__restrict__ x, int64_t T, int64_t K, int64_t k0,
+                                         int64_t Kc, int64_t L, int ref, int64_t mask_s, double *R) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= L) return;
+    const bool live = t < T && t % mask_s == 0;
+    for (int64_t c = 0; c < Kc; ++c) {
+        const int64_t k = k0 + c;
+        float v = 0.f;
+        if (live && k < K) {
+            v = x[t * K + k];
+            if (ref) v -= x[k];
+        }
+        R[c * L + t] = static_cast<double>(v);
+    }
+}
+
 // C <- |C|^2 (s = 1) or conj(Cm) C (s > 1): the transform of the lag sums.
 __global__ void fft_power_kernel(cufftDoubleComplex *C, const cufftDoubleComplex *Cm, int64_t n) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -268,11 +288,16 @@ int fft_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, i
     for (int64_t ch = 0; ch < F.n_chunks; ++ch) {
         const int64_t k0 = ch * F.Kc;
         const dim3 g(static_cast<unsigned>(ceil_div(F.L, 32)), static_cast<unsigned>(ceil_div(F.Kc, 32)));
+        const unsigned gn = static_cast<unsigned>(ceil_div(F.L, 256));
+        auto gather = [&](const float *src, int64_t mask_s, double *dst) {
+            if (F.Kc <= kNarrowGather)
+                fft_gather_narrow_kernel<<<gn, 256, 0, st>>>(src, T, F.K, k0, F.Kc, F.L, kind == 0, mask_s, dst);
+            else
+                fft_gather_kernel<<<g, dim3(32, 8), 0, st>>>(src, T, F.K, k0, F.Kc, F.L, kind == 0, mask_s, dst);
+        };
         // later side: B (cross) or the signal itself; origin side: the signal, masked to sZ
-        fft_gather_kernel<<<g, dim3(32, 8), 0, st>>>(kind == 2 ? d_y : d_x, T, F.K, k0, F.Kc, F.L, kind == 0, 1,
-                                                     R);
-        if (two)
-            fft_gather_kernel<<<g, dim3(32, 8), 0, st>>>(d_x, T, F.K, k0, F.Kc, F.L, kind == 0, s, Rm);
+        gather(kind == 2 ? d_y : d_x, 1, R);
+        if (two) gather(d_x, s, Rm);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fft_gather launch");
         if (cufftExecD2Z(fwd.h, R, C) != CUFFT_SUCCESS) return TCORR_ECUDA;
         if (two && cufftExecD2Z(fwd.h, Rm, Cm) != CUFFT_SUCCESS) return TCORR_ECUDA;
