@@ -153,7 +153,7 @@ def gpu_identifier(torch, dev):
 # DRAM bytes (read + write) of one water-scale MSD launch of the tensor-core band kernel (FP16 x3),
 # from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
 # see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
-GRAM_WATER_TRAFFIC_BYTES = 8 * (982.338816e6 + 5.912576e6)
+GRAM_WATER_TRAFFIC_BYTES = 8 * (982.413568e6 + 5.242112e6)
 
 
 def peaks():
