@@ -821,8 +821,16 @@ struct SplitDesc {
     float *inv_scale;
     double *S;
     int kind, vec;
-    int64_t blk_begin;        // batch: first global block (frame x group) of this instance
+    int warp_mode;            // groups of at most kWarpSeg columns: one warp per (frame, group)
+    int64_t blk_begin;        // batch: first global block of this instance
 };
+
+// Groups of up to kWarpSeg columns (small K) are split by one warp each,
+// eight frames per block: a 256-thread block per (frame, group) would leave
+// most lanes idle and spend more on its reductions than on the data.
+constexpr int64_t kWarpSeg = 1024;
+constexpr int kWarpFrames = PREP_THREADS / 32;
+
 
 // Block-wide max of |x| -> power-of-two scale 2^e with max |x| 2^e < 2^14,
 // so that FP16 hi and lo stay normal; stores 2^-e for the epilogue.
@@ -952,12 +960,83 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
     }
 }
 
+// One warp per (frame t, K-group g) of at most kWarpSeg columns: the same
+// values as split_body, with warp shuffles in place of block reductions.
+template <int PREC, int KIND, bool VEC>
+__device__ __forceinline__ void split_warp_body(const SplitDesc &q, int64_t t, int64_t g) {
+    if (t >= q.T_pad) return;                  // past the last padded frame (whole warp)
+    const int lane = threadIdx.x & 31;
+    const float *X = q.X;
+    const bool live = t < q.T;
+    const float *row = X + (live ? t : 0) * q.K;
+    const int64_t Klive = live ? q.K : 0;
+    const int64_t kb = g * q.kseg;
+    const int64_t ke = g == q.n_groups - 1 ? q.Kp : min(q.Kp, kb + q.kseg);
+    constexpr int NCW = static_cast<int>(kWarpSeg / 256);    // 8 columns per lane per chunk
+    float x[NCW][8];
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCW; ++c) {
+        const int64_t k0 = kb + c * 256 + lane * 8;
+        if (k0 < ke) {
+            load8<KIND, VEC>(row, X, k0, Klive, x[c]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[c][i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(x[c][i]));
+    }
+    float scale = 1.f;
+    if (PREC == P_FP16) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        int e = 0;
+        if (mx > 0.f) {
+            int ex;
+            frexpf(mx, &ex);
+            e = 14 - ex;
+            e = e < -60 ? -60 : (e > 60 ? 60 : e);
+        }
+        scale = ldexpf(1.f, e);
+        if (lane == 0) q.inv_scale[g * q.T_pad + t] = ldexpf(1.f, -e);
+    }
+    double sacc = 0.0;
+#pragma unroll
+    for (int c = 0; c < NCW; ++c) {
+        const int64_t k0 = kb + c * 256 + lane * 8;
+        if (k0 < ke) {
+            if (KIND == 0) {
+                float sq = 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) sq = fmaf(x[c][i], x[c][i], sq);
+                sacc += static_cast<double>(sq);
+            }
+            split_store8<PREC>(x[c], scale, q.Xh, q.Xl, t * q.Kp + k0);
+        }
+    }
+    if (KIND == 0 && q.S != nullptr) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+        if (lane == 0 && live) q.S[g * q.T + t] = sacc;
+    }
+}
+
 template <int PREC, int KIND, bool VEC>
 __global__ void __launch_bounds__(PREP_THREADS, 2) split_kernel(const __grid_constant__ SplitDesc q) {
     split_body<PREC, KIND, VEC>(q, blockIdx.x, blockIdx.y);
 }
 
-template <int PREC>
+template <int PREC, int KIND, bool VEC>
+__global__ void __launch_bounds__(PREP_THREADS, 2) split_warp_kernel(const __grid_constant__ SplitDesc q) {
+    split_warp_body<PREC, KIND, VEC>(q, static_cast<int64_t>(blockIdx.x) * kWarpFrames + (threadIdx.x >> 5),
+                                     blockIdx.y);
+}
+
+// Batch: the instances of one prep class (kind, float4 loads, warp mode) in
+// one grid, block -> instance by binary search; each class is its own
+// specialisation, so the kernel carries only the registers its class needs.
+template <int PREC, int KIND, bool VEC, bool WARP>
 __global__ void __launch_bounds__(PREP_THREADS, 2) split_batch_kernel(const SplitDesc *__restrict__ d, int n) {
     const int64_t b = blockIdx.x;
     int lo = 0, hi = n - 1;
@@ -968,14 +1047,9 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) split_batch_kernel(const Spli
     }
     const SplitDesc &q = d[lo];
     const int64_t local = b - q.blk_begin;
-    const int64_t t = local / q.n_groups, g = local - t * q.n_groups;
-    if (q.kind == 0) {
-        if (q.vec) split_body<PREC, 0, true>(q, t, g);
-        else split_body<PREC, 0, false>(q, t, g);
-    } else {
-        if (q.vec) split_body<PREC, 1, true>(q, t, g);
-        else split_body<PREC, 1, false>(q, t, g);
-    }
+    const int64_t tb = local / q.n_groups, g = local - tb * q.n_groups;
+    if (WARP) split_warp_body<PREC, KIND, VEC>(q, tb * kWarpFrames + (threadIdx.x >> 5), g);
+    else split_body<PREC, KIND, VEC>(q, tb, g);
 }
 
 // prefix[rho][j] = sum_{j' < j} S(rho + j' s), j = 0 .. n_rho.  One block per
@@ -1050,7 +1124,25 @@ struct PfxDesc {
     int64_t T, n_groups, s, pstride;
     double *prefix;
     int64_t blk_begin;        // first global block (residue) of this instance
+    int64_t frame_begin;      // first global frame of this instance (S combine pass)
 };
+
+// Batch: S[0][f] = sum over groups of S[g][f] for every frame of every MSD
+// instance, one thread per (instance, frame).
+__global__ void s_combine_batch_kernel(const PfxDesc *__restrict__ d, int n, int64_t total) {
+    const int64_t f = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (f >= total) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].frame_begin <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    const PfxDesc &q = d[lo];
+    double *S = const_cast<double *>(q.S);
+    const int64_t t = f - q.frame_begin;
+    S[t] = s_total(S, q.T, q.n_groups, t);
+}
 
 __global__ void __launch_bounds__(PFX_THREADS) s_prefix_batch_kernel(const PfxDesc *__restrict__ d, int n) {
     const int64_t b = blockIdx.x;
@@ -1499,6 +1591,18 @@ cudaError_t launch_gram_batch(const SrcBatch &src, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Prep mode of a layout: one warp per (frame, group) when no group is longer
+// than kWarpSeg columns (the last group runs to Kp), else one block.
+bool split_warp_mode(const GramLayout &L) {
+    const int64_t kseg = (L.kseg / L.bke) * L.bke;
+    const int64_t last = L.Kp - (L.p.n_groups - 1) * kseg;
+    return (kseg > last ? kseg : last) <= kWarpSeg;
+}
+
+int64_t split_block_count(const GramLayout &L) {
+    return split_warp_mode(L) ? ceil_div(L.T_pad, kWarpFrames) * L.p.n_groups : L.T_pad * L.p.n_groups;
+}
+
 SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *base, int64_t blk_begin) {
     SplitDesc q;
     q.X = X;
@@ -1514,6 +1618,7 @@ SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *bas
     q.S = kind == 0 ? reinterpret_cast<double *>(base + L.off_S) : nullptr;
     q.kind = kind;
     q.vec = (q.K % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+    q.warp_mode = split_warp_mode(L) ? 1 : 0;
     q.blk_begin = blk_begin;
     return q;
 }
@@ -1521,6 +1626,17 @@ SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *bas
 template <int PREC>
 cudaError_t launch_split(const SplitDesc &q, cudaStream_t st) {
     if (q.n_groups > 65535 || q.T_pad > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (q.warp_mode) {
+        const dim3 gw(static_cast<unsigned>(ceil_div(q.T_pad, kWarpFrames)), static_cast<unsigned>(q.n_groups));
+        if (q.kind == 0) {
+            if (q.vec) split_warp_kernel<PREC, 0, true><<<gw, PREP_THREADS, 0, st>>>(q);
+            else split_warp_kernel<PREC, 0, false><<<gw, PREP_THREADS, 0, st>>>(q);
+        } else {
+            if (q.vec) split_warp_kernel<PREC, 1, true><<<gw, PREP_THREADS, 0, st>>>(q);
+            else split_warp_kernel<PREC, 1, false><<<gw, PREP_THREADS, 0, st>>>(q);
+        }
+        return cudaGetLastError();
+    }
     const dim3 g(static_cast<unsigned>(q.T_pad), static_cast<unsigned>(q.n_groups));
     if (q.kind == 0) {
         if (q.vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(q);
@@ -1528,6 +1644,27 @@ cudaError_t launch_split(const SplitDesc &q, cudaStream_t st) {
     } else {
         if (q.vec) split_kernel<PREC, 1, true><<<g, PREP_THREADS, 0, st>>>(q);
         else split_kernel<PREC, 1, false><<<g, PREP_THREADS, 0, st>>>(q);
+    }
+    return cudaGetLastError();
+}
+
+// Prep class of a batch entry: kind (0 MSD, 1 ACF), float4 loads, warp mode.
+int split_class(const SplitDesc &q) { return q.kind * 4 + q.vec * 2 + q.warp_mode; }
+
+template <int PREC>
+cudaError_t launch_split_batch_class(int cls, const SplitDesc *d, int n, int64_t blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const unsigned g = static_cast<unsigned>(blocks);
+    switch (cls) {
+        case 0: split_batch_kernel<PREC, 0, false, false><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        case 1: split_batch_kernel<PREC, 0, false, true><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        case 2: split_batch_kernel<PREC, 0, true, false><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        case 3: split_batch_kernel<PREC, 0, true, true><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        case 4: split_batch_kernel<PREC, 1, false, false><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        case 5: split_batch_kernel<PREC, 1, false, true><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        case 6: split_batch_kernel<PREC, 1, true, false><<<g, PREP_THREADS, 0, st>>>(d, n); break;
+        default: split_batch_kernel<PREC, 1, true, true><<<g, PREP_THREADS, 0, st>>>(d, n); break;
     }
     return cudaGetLastError();
 }
@@ -1645,7 +1782,7 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     };
     B->off_inst = take(sizeof(InstDesc) * count);
     B->off_split = take(sizeof(SplitDesc) * count);
-    B->off_pfx = take(sizeof(PfxDesc) * (B->n_msd > 0 ? B->n_msd : 1));
+    B->off_pfx = take(2 * sizeof(PfxDesc) * (B->n_msd > 0 ? B->n_msd : 1));   // combine, then prefix
     B->off_red = take(sizeof(LagReduceDesc) * count);
     B->off_counter = take(sizeof(unsigned long long));
     B->off_pprep = take(sizeof(PolyPrepArgs) * count);
@@ -1657,7 +1794,7 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
         B->base[i] = take(B->L[i].total);
         if (B->L[i].poly) continue;      // polyphase instances have prep and reduction of their own
         B->total_items += B->L[i].p.n_items;
-        B->total_frames += B->L[i].T_pad * B->L[i].p.n_groups;     // prep blocks: frame x K-group
+        B->total_frames += split_block_count(B->L[i]);             // prep blocks
         if (items[i].kind == 0) B->total_pfx += B->L[i].p.n_res;
         B->total_lags += items[i].tau_max + 1;
     }
@@ -2021,7 +2158,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     std::vector<PfxDesc> pfx;
     std::vector<LagReduceDesc> red(count);
     std::vector<InstDesc> big_desc;
-    int64_t item_begin = 0, frame_begin = 0, pfx_begin = 0, lag_begin = 0;
+    int64_t item_begin = 0, frame_begin = 0, pfx_begin = 0, lag_begin = 0, s_frames = 0;
     std::vector<PolyPrepArgs> pprep;
     std::vector<PolyReduceArgs> pred;
     std::vector<int> poly_msd;
@@ -2068,7 +2205,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             inst.push_back(d);
         }
         spl[nb] = split_desc(it.kind, it.d_x, L, base, frame_begin);
-        frame_begin += L.T_pad * L.p.n_groups;
+        frame_begin += split_block_count(L);
         if (it.kind == 0) {
             PfxDesc q;
             q.S = reinterpret_cast<const double *>(base + L.off_S);
@@ -2078,6 +2215,8 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             q.pstride = L.pstride;
             q.prefix = reinterpret_cast<double *>(base + L.off_prefix);
             q.blk_begin = pfx_begin;
+            q.frame_begin = s_frames;
+            s_frames += it.T;
             pfx_begin += L.p.n_res;
             pfx.push_back(q);
         }
@@ -2085,13 +2224,34 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
         lag_begin += it.tau_max + 1;
         ++nb;
     }
+    // the prefix pass reads S after the group parts were combined into group 0
+    std::vector<PfxDesc> pfx1(pfx);
+    for (PfxDesc &q : pfx1) q.n_groups = 1;
+    // prep descriptors grouped by class, block offsets counted within each class
+    std::vector<SplitDesc> spl_by_class;
+    int cls_start[9] = {0};
+    int64_t cls_blocks[8] = {0};
+    for (int c = 0; c < 8; ++c) {
+        cls_start[c] = static_cast<int>(spl_by_class.size());
+        for (int k = 0; k < nb; ++k) {
+            if (split_class(spl[k]) != c) continue;
+            SplitDesc q = spl[k];
+            q.blk_begin = cls_blocks[c];
+            cls_blocks[c] += q.warp_mode ? ceil_div(q.T_pad, kWarpFrames) * q.n_groups : q.T_pad * q.n_groups;
+            spl_by_class.push_back(q);
+        }
+    }
+    cls_start[8] = static_cast<int>(spl_by_class.size());
     const int np = static_cast<int>(pprep.size());
     cudaError_t e = cudaSuccess;
     if ((!inst.empty() &&
          (e = upload_bytes(ws + B.off_inst, inst.data(), sizeof(InstDesc) * inst.size(), st)) != cudaSuccess) ||
-        (nb > 0 && (e = upload_bytes(ws + B.off_split, spl.data(), sizeof(SplitDesc) * nb, st)) != cudaSuccess) ||
+        (nb > 0 &&
+         (e = upload_bytes(ws + B.off_split, spl_by_class.data(), sizeof(SplitDesc) * nb, st)) != cudaSuccess) ||
         (nb > 0 && (e = upload_bytes(ws + B.off_red, red.data(), sizeof(LagReduceDesc) * nb, st)) != cudaSuccess) ||
         (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx, pfx.data(), sizeof(PfxDesc) * pfx.size(), st)) != cudaSuccess) ||
+        (!pfx.empty() && (e = upload_bytes(ws + B.off_pfx + sizeof(PfxDesc) * pfx.size(), pfx1.data(),
+                                           sizeof(PfxDesc) * pfx1.size(), st)) != cudaSuccess) ||
         (np > 0 && (e = upload_bytes(ws + B.off_pprep, pprep.data(), sizeof(PolyPrepArgs) * np, st)) != cudaSuccess) ||
         (np > 0 && (e = upload_bytes(ws + B.off_pred, pred.data(), sizeof(PolyReduceArgs) * np, st)) != cudaSuccess))
         return cuda_fail(e, "descriptor upload");
@@ -2111,16 +2271,27 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
     }
 
     const SplitDesc *d_spl = reinterpret_cast<const SplitDesc *>(ws + B.off_split);
-    const unsigned gs = static_cast<unsigned>(B.total_frames);
-    if (nb > 0) switch (B.prec) {
-        case P_FP16: split_batch_kernel<P_FP16><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
-        case P_BF16: split_batch_kernel<P_BF16><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
-        default: split_batch_kernel<P_TF32><<<gs, PREP_THREADS, 0, st>>>(d_spl, nb); break;
+    for (int c = 0; c < 8; ++c) {
+        const int n = cls_start[c + 1] - cls_start[c];
+        if (n == 0) continue;
+        const SplitDesc *dc = d_spl + cls_start[c];
+        switch (B.prec) {
+            case P_FP16: e = launch_split_batch_class<P_FP16>(c, dc, n, cls_blocks[c], st); break;
+            case P_BF16: e = launch_split_batch_class<P_BF16>(c, dc, n, cls_blocks[c], st); break;
+            default: e = launch_split_batch_class<P_TF32>(c, dc, n, cls_blocks[c], st); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "split_batch_kernel launch");
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split_batch_kernel launch");
     if (!pfx.empty()) {
+        // the group parts of S(t) are combined in parallel (in place, into group 0),
+        // then the prefix pass reads one value per frame (its descriptors say 1 group)
+        const PfxDesc *d_pfx = reinterpret_cast<const PfxDesc *>(ws + B.off_pfx);
+        s_combine_batch_kernel<<<static_cast<unsigned>(ceil_div(s_frames, 256)), 256, 0, st>>>(
+            d_pfx, static_cast<int>(pfx.size()), s_frames);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "s_combine_batch_kernel launch");
         s_prefix_batch_kernel<<<static_cast<unsigned>(B.total_pfx), PFX_THREADS, 0, st>>>(
-            reinterpret_cast<const PfxDesc *>(ws + B.off_pfx), static_cast<int>(pfx.size()));
+            reinterpret_cast<const PfxDesc *>(ws + B.off_pfx + sizeof(PfxDesc) * pfx.size()),
+            static_cast<int>(pfx.size()));
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "s_prefix_batch_kernel launch");
     }
     for (const InstDesc &d : big_desc) {
