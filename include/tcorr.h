@@ -81,7 +81,7 @@ typedef enum {
        x = hi + lo, products hi.hi + hi.lo + lo.hi (x3) or also lo.lo (x4),
        FP32 accumulation in TMEM, FP64 per-lag sums.  The MSD is assembled as
        S(t0) + S(t0+tau) - 2 G(t0, t0+tau) with S(t) = |x_t|^2 in FP64, after
-       referencing positions to frame 0.  Accuracy target: 1e-5 relative to
+       referencing positions to the middle frame.  Accuracy target: 1e-5 relative to
        C(0) or MSD(tau_max). */
     TCORR_TC_TF32X3 = 1,
     TCORR_TC_BF16X3 = 2,

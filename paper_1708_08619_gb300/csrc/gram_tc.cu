@@ -7,8 +7,8 @@
 // where D(tau) sums the Gram entries G(t0, t0+tau) = x_{t0} . x_{t0+tau}
 // along one band offset, P(tau) = sum_{t0} S(t0), Q(tau) = sum_{t0} S(t0+tau)
 // and S(t) = |x_t|^2 (expanding |a - b|^2 = |a|^2 + |b|^2 - 2 a.b).  For the
-// MSD the positions are first referenced to frame 0 (x_t = r_t - r_0; the MSD
-// only sees differences) so that S and G stay small.
+// MSD the positions are first referenced to the middle frame m (x_t = r_t - r_m;
+// the MSD only sees differences) so that S and G stay small.
 //
 // Split precision: each FP32 value is written as x = hi + lo with hi and lo in
 // a 16-bit (or TF32) format and G is accumulated from hi.hi + hi.lo + lo.hi
@@ -79,15 +79,28 @@ constexpr int NEPI = 8;          // epilogue warps
 constexpr uint32_t TMEM_COLS = 512;
 // K-blocks per TMEM accumulation sub-chain (defaults).  The tensor core's FP32
 // accumulation drifts low by about the same amount per accumulate step, so the
-// error grows linearly with the chain (water-scale MSD: 2.6 / 3.5 / 5.5 e-6 of
-// MSD(tau_max) at 3 / 4 / 6 K-blocks) while longer chains hand fewer partial
-// sums to the epilogue (18.66 / 17.94 / 17.40 ms per step).  Band form: 4;
-// polyphase (flux ACF 1.3e-6 of C(0) at 6, 9.5% faster than at 3): 6.
-constexpr int kSubKb = 4;
-constexpr int kSubKbPoly = 6;
+// error grows linearly with the chain while longer chains hand fewer partial
+// sums to the epilogue.  The MSD is assembled as P + Q - 2D with D several
+// times MSD(tau_max), which multiplies the drift: referenced to frame 0 the
+// water-scale MSD erred 3.8 / 8.2 e-6 of MSD(tau_max) at 4 / 8 K-blocks;
+// referenced to the middle frame 1.8 / 2.9 / 4.0 e-6 at 4 / 6 / 8 K-blocks
+// (launch 7.67 / 7.21 / 7.08 ms).  A correlation is compared with C(0)
+// directly (water-scale VACF 0.76 / 1.47 / 2.42 / 3.10 e-6 of C(0) at
+// 4 / 8 / 12 / 16 K-blocks, launch 7.70 / 7.41 / 7.27 / 7.18 ms; flux ACF
+// 1.3 / 1.7 / 2.7 / 3.6 e-6 at 6 / 8 / 12 / 16, step 8.84 / 8.29 / 7.66 /
+// 7.38 ms).
+// Chain lengths are set by accuracy per kind, not tuned for speed.
+constexpr int kSubKb = 8;          // band form, MSD
+constexpr int kSubKbCorr = 12;     // band form, auto- and cross-correlation
+constexpr int kSubKbPoly = 12;     // polyphase form (correlations only)
+
+int default_sub_kb(int kind, bool poly) {
+    if (poly) return kSubKbPoly;
+    return kind == 0 ? kSubKb : kSubKbCorr;
+}
 
 // Manual overrides: TCORR_KSEG (K elements per work item, a multiple of 64)
-// and TCORR_SUB_KB (K-blocks per accumulation sub-chain, 1..8).  Longer
+// and TCORR_SUB_KB (K-blocks per accumulation sub-chain, 1..16).  Longer
 // sub-chains trade accuracy for fewer accumulator hand-offs.
 int64_t env_kseg() {
     const char *e = std::getenv("TCORR_KSEG");
@@ -97,7 +110,7 @@ int64_t env_kseg() {
 int env_sub_kb() {
     const char *e = std::getenv("TCORR_SUB_KB");
     const int v = e ? std::atoi(e) : 0;
-    return (v >= 1 && v <= 8) ? v : 0;
+    return (v >= 1 && v <= 16) ? v : 0;
 }
 
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -730,7 +743,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_band_batch_kernel(const __gr
 }
 
 // ------------------------------------------------------------------ prep
-// One block per padded frame row t.  x = X[t] - X[0] (MSD) or X[t] (ACF);
+// One block per padded frame row t.  x = X[t] - X[m] (MSD, m the middle frame) or X[t] (ACF);
 // FP16 rows are scaled by 2^e_t with e_t chosen so max |x| * 2^e_t < 2^14.
 constexpr int PREP_THREADS = 256;
 
@@ -786,7 +799,7 @@ __device__ __forceinline__ void split_store8(const float (&x)[8], float scale, v
     }
 }
 
-// Eight consecutive values x = X[t][k..k+7] (- X[0][k..k+7] for the MSD),
+// Eight consecutive values x = X[t][k..k+7] (- ref[k..k+7] for the MSD),
 // zero past K.  VEC: rows are 16-byte aligned and K % 4 == 0 (float4 loads).
 template <int KIND, bool VEC>
 __device__ __forceinline__ void load8(const float *__restrict__ row, const float *__restrict__ ref, int64_t k,
@@ -816,6 +829,7 @@ __device__ __forceinline__ void load8(const float *__restrict__ row, const float
 // partial of S(t) are kept per (group, frame): inv_scale[g][T_pad], S[g][T].
 struct SplitDesc {
     const float *X;
+    const float *ref;         // MSD: the reference frame's row (the middle frame)
     int64_t T, K, Kp, T_pad, kseg, n_groups;
     void *Xh, *Xl;
     float *inv_scale;
@@ -854,7 +868,7 @@ __device__ __forceinline__ float fp16_scale(float mx, float *red_f, float *inv_o
     return ldexpf(1.f, e);
 }
 
-// One block per (padded frame t, K-group g): x = r_t - r_0 (MSD) or A_t
+// One block per (padded frame t, K-group g): x = r_t - r_m (MSD) or A_t
 // (ACF) over the group's columns, scaled (FP16) and split into hi/lo, and the
 // group's part of S(t) = |x_t|^2 in FP64.  A group of up to 8 x 2048 columns
 // is held in registers: one read from DRAM, then the max, then the stores.
@@ -877,7 +891,7 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
     if (ke - kb <= NCH * STEP) {
         float x[NCH][8];
         float mx = 0.f;
-        // MSD: the frame-0 values are loaded with their rows, half the chunks at a
+        // MSD: the reference frame's values are loaded with their rows, half the chunks at a
         // time, so that the loads in flight fit the registers
         constexpr int NH = KIND == 0 ? NCH / 2 : NCH;
 #pragma unroll
@@ -889,7 +903,7 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
                 const int64_t k0 = kb + c * STEP + static_cast<int64_t>(tid) * 8;
                 if (k0 < ke) {
                     load8<1, VEC>(row, X, k0, Klive, x[c]);
-                    if (KIND == 0) load8<1, VEC>(X, X, k0, Klive, r[cc]);
+                    if (KIND == 0) load8<1, VEC>(q.ref, q.ref, k0, Klive, r[cc]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -928,7 +942,7 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
             float mx = 0.f;
             for (int64_t k0 = kb + static_cast<int64_t>(tid) * 8; k0 < ke; k0 += STEP) {
                 float x[8];
-                load8<KIND, VEC>(row, X, k0, Klive, x);
+                load8<KIND, VEC>(row, q.ref, k0, Klive, x);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(x[i]));
             }
@@ -936,7 +950,7 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
         }
         for (int64_t k0 = kb + static_cast<int64_t>(tid) * 8; k0 < ke; k0 += STEP) {
             float x[8];
-            load8<KIND, VEC>(row, X, k0, Klive, x);
+            load8<KIND, VEC>(row, q.ref, k0, Klive, x);
             if (KIND == 0) {
                 float sq = 0.f;
 #pragma unroll
@@ -979,7 +993,7 @@ __device__ __forceinline__ void split_warp_body(const SplitDesc &q, int64_t t, i
     for (int c = 0; c < NCW; ++c) {
         const int64_t k0 = kb + c * 256 + lane * 8;
         if (k0 < ke) {
-            load8<KIND, VEC>(row, X, k0, Klive, x[c]);
+            load8<KIND, VEC>(row, q.ref, k0, Klive, x[c]);
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) x[c][i] = 0.f;
@@ -1428,9 +1442,10 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
     if (L->Kalloc >= (int64_t(1) << 31)) return false;
     const int64_t kb_total = ceil_div(L->Kprime, L->bke);
     {
-        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq), kSubKbPoly};
+        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq), 0};
         if (const TuneChoice *o = get_tune_override()) c = *o;
         if (const int64_t ek = env_kseg()) c.kseg = ek;
+        if (c.sub_kb <= 0) c.sub_kb = default_sub_kb(kind, true);
         if (const int es = env_sub_kb()) c.sub_kb = es;
         L->kseg = c.kseg;
         L->sub_kb = c.sub_kb;
@@ -1495,11 +1510,12 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     {
         const BandPlan p0 = make_band_plan(T, N, tau_max, s, BO, BF, 64, 1);
         const int64_t tiles = p0.n_res * p0.n_rows * p0.n_cols;
-        TuneChoice c{tune_default_kseg(K, tiles), kSubKb};
+        TuneChoice c{tune_default_kseg(K, tiles), 0};
         TuneChoice cached;
         if (const TuneChoice *o = get_tune_override()) c = *o;
         else if (tune_mode() != 0 && tune_lookup(tune_key(method, kind, K, tau_max, T, s), &cached)) c = cached;
         if (const int64_t ek = env_kseg()) c.kseg = ek;
+        if (c.sub_kb <= 0) c.sub_kb = default_sub_kb(kind, false);
         if (const int es = env_sub_kb()) c.sub_kb = es;
         L->kseg = c.kseg;
         L->sub_kb = c.sub_kb;
@@ -1603,9 +1619,17 @@ int64_t split_block_count(const GramLayout &L) {
     return split_warp_mode(L) ? ceil_div(L.T_pad, kWarpFrames) * L.p.n_groups : L.T_pad * L.p.n_groups;
 }
 
+// The MSD is unchanged by a constant shift of an atom's positions, so any
+// frame may serve as the reference x_t = r_t - r_ref.  The middle frame keeps
+// |x_t|^2, and with it the Gram sum D that P + Q - 2D cancels, about half as
+// large as frame 0 does for a diffusive walk (a quarter for ballistic motion),
+// which halves the effect of the tensor core's accumulation drift on the MSD.
+int64_t msd_ref_frame(int64_t T) { return (T - 1) / 2; }
+
 SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *base, int64_t blk_begin) {
     SplitDesc q;
     q.X = X;
+    q.ref = X + msd_ref_frame(L.p.T) * L.p.K;
     q.T = L.p.T;
     q.K = L.p.K;
     q.Kp = L.Kp;
@@ -1982,7 +2006,7 @@ size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int
     if (!make_layout(T, N, tau_max, s, method, kind, &L, w)) return 0;
     size_t need = L.total;
     if (!w && tune_mode() != 0) {
-        const TuneChoice shortest{tune_min_kseg(), kSubKb};
+        const TuneChoice shortest{tune_min_kseg(), 0};
         const TuneChoice *prev = get_tune_override();
         set_tune_override(&shortest);
         GramLayout Ls;
@@ -2069,7 +2093,8 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     return TCORR_OK;
 }
 
-// Times every tuning candidate on the stream (synchronising) and keeps the fastest.
+// Times every tuning candidate (work-item length; the sub-chain length stays
+// the kind's default) on the stream, synchronising, and keeps the fastest.
 int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s,
               int method, double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, TuneChoice *best,
               const float *d_y) {

@@ -105,7 +105,8 @@ inline int cuda_fail(cudaError_t e, const char *what) {
 }
 
 // Autotuner (tune.cu): per shape bucket, the tensor-core work-item length
-// (kseg, K elements) and accumulation sub-chain length (sub_kb, K-blocks).
+// (kseg, K elements) and accumulation sub-chain length (sub_kb, K-blocks;
+// 0 = the default for the kind and form).
 struct TuneChoice {
     int64_t kseg;
     int sub_kb;

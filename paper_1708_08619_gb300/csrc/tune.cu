@@ -3,8 +3,10 @@
 //             fewer items pay fewer end-of-item reductions);
 //   sub_kb -- K-blocks per TMEM accumulation sub-chain (longer chains hand
 //             the accumulator over less often but lose more low bits).
-// Without TCORR_TUNE the library uses a heuristic (tune_default_kseg) and a
-// fixed sub-chain length.  With TCORR_TUNE=1 the first call for a shape
+// Only kseg is timed: sub_kb decides the accuracy, so the candidates leave it
+// at 0, which stands for the kind's default (a cached nonzero sub_kb, written
+// by hand or by an older library, is honoured).  Without TCORR_TUNE the
+// library uses a heuristic (tune_default_kseg).  With TCORR_TUNE=1 the first call for a shape
 // bucket times every candidate on the caller's stream (this synchronises,
 // so it is skipped while the stream is being captured) and remembers the
 // fastest; TCORR_TUNE=force re-times on every call.  TCORR_TUNE_CACHE names
@@ -92,7 +94,7 @@ void tune_store(const std::string &key, const TuneChoice &c) {
 }
 
 const std::vector<TuneChoice> &tune_candidates() {
-    static const std::vector<TuneChoice> c = {{4096, 3}, {8192, 3}, {16384, 3}, {8192, 2}, {16384, 4}};
+    static const std::vector<TuneChoice> c = {{4096, 0}, {8192, 0}, {16384, 0}};
     return c;
 }
 
