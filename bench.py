@@ -153,7 +153,7 @@ def gpu_identifier(torch, dev):
 # DRAM bytes (read + write) of one water-scale MSD launch of the tensor-core band kernel (FP16 x3),
 # from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
 # see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
-GRAM_WATER_TRAFFIC_BYTES = 8 * (982.413568e6 + 5.242112e6)
+GRAM_WATER_TRAFFIC_BYTES = 8 * (982.221568e6 + 5.485568e6)
 
 
 def peaks():
@@ -386,6 +386,15 @@ def run_gpu(args, wl):
 
     e2e_stream_s = timed_e2e(e2e_streamed)
     del ws_a, ws_b
+    # the input buffers' own host link rate: one whole-array copy of the
+    # positions (same values as the resident array), CUDA events
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    with torch.cuda.stream(stream):
+        x.copy_(xh, non_blocking=True)
+    i1.record(stream)
+    i1.synchronize()
+    h2d_gbs_input = xh.numel() * 4 / (i0.elapsed_time(i1) / 1e3) / 1e9
     # this machine's host link: one pinned-to-device copy of 1 GiB, CUDA events
     hb = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
     db = torch.empty(1 << 28, dtype=torch.float32, device=dev)
@@ -408,6 +417,7 @@ def run_gpu(args, wl):
                 "streamed_ms_per_step": e2e_stream_s * 1e3,
                 "incore_ms_per_step": e2e_incore_s * 1e3,
                 "h2d_gbs_measured": h2d_gbs,
+                "h2d_gbs_input_buffer": h2d_gbs_input,
                 "h2d_link_bound_ms": h2d / h2d_gbs / 1e6}
 
     # ---- roofline of the dominant kernel (the MSD band kernel), timed alone
