@@ -582,13 +582,22 @@ def run_batch_workload(args, wl):
                 f(x, tm, s, method, out=out, ws=ws1, stream=stream)
         per_instance()
         stream.synchronize()
-        e0.record(stream)
-        reps = max(1, min(3, args.steps))
-        for _ in range(reps):
-            per_instance()
-        e1.record(stream)
-        stream.synchronize()
-        single_ms = e0.elapsed_time(e1) / reps
+        # the comparison alternates the two forms (batch, per-instance, batch, ...) so that both
+        # see the same power-cap state; medians of the pairs
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        pair_b, pair_p = [], []
+        for _ in range(max(1, min(3, args.steps))):
+            for fn, acc in ((lambda: tcorr.tcorr_batch(inst, method, ws=ws, stream=stream), pair_b),
+                            (per_instance, pair_p)):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                fn()
+                a1.record(stream)
+                a1.synchronize()
+                acc.append(a0.elapsed_time(a1))
+        del ws
+        single_ms = statistics.median(pair_p)
+        batch_pair_ms = statistics.median(pair_b)
     ms = shard.max_over_ranks(batch_ms)
     value = u_total / (ms / 1000.0)            # the whole batch, shared by all ranks
     pk, pk_kind = peaks()
@@ -600,8 +609,10 @@ def run_batch_workload(args, wl):
             "config": {"workload": wl["label"], "instances": wl["count"], "method": method,
                        "parallelism": f"instance-sharded x{world} (greedy by work, no exchange)",
                        "updates_per_step": u_total, "input_gb": sum(x.numel() * 4 for _, x, *_ in items) / 1e9,
-                       "per_instance_launches_ms": single_ms, "graph_batch_ms": batch_ms,
-                       "batch_speedup_vs_per_instance": single_ms / batch_ms,
+                       "graph_batch_ms": batch_ms, "workspace_gb": need / 1e9,
+                       "alternating_pairs": {"graph_batch_ms": batch_pair_ms, "per_instance_launches_ms": single_ms,
+                                             "pairs": len(pair_p)},
+                       "batch_speedup_vs_per_instance": single_ms / batch_pair_ms,
                        "l2": "inputs larger than L2, no flush"},
             "clocks": clocks, "e2e": None,
             "gpu_launches": None,
@@ -642,9 +653,10 @@ def run_flux_workload(args, wl):
     stream = torch.cuda.Stream(dev)
     res = {}
     for method in ((args.method,) if args.no_plain_compare else (args.method, "plain")):
-        outs = [torch.empty(tm + 1, dtype=torch.float64, device=dev) for _ in range(1 + wl["nshort"])]
-        gks = [torch.empty(tm + 1, dtype=torch.float64, device=dev) for _ in range(1 + wl["nshort"])]
-        items = [(1, x, tm, 1, o) for x, o in zip(xs, outs[1:])]
+        # one row per series (the long one first): the running integrals of all of them in one launch
+        outs = torch.empty((1 + wl["nshort"], tm + 1), dtype=torch.float64, device=dev)
+        gks = torch.empty_like(outs)
+        items = [(1, x, tm, 1, outs[1 + i]) for i, x in enumerate(xs)]
         inst = tcorr.make_instances(items)
         ws_b = torch.empty(max(256, tcorr.tcorr_batch_workspace_size(inst, method)), dtype=torch.uint8, device=dev)
         ws_l = torch.empty(max(256, tcorr.tcorr_workspace_size(wl["T"], 1, tm, 1, method)), dtype=torch.uint8,
@@ -653,8 +665,7 @@ def run_flux_workload(args, wl):
             def step():
                 tcorr.tcorr_acf(xl, tm, 1, method, out=outs[0], ws=ws_l, stream=stream)
                 tcorr.tcorr_batch(inst, method, ws=ws_b, stream=stream)
-                for o, g in zip(outs, gks):
-                    tcorr.gk_integrate(o, 1.0, 1.0 / 3.0, out=g, stream=stream)
+                tcorr.gk_integrate_batch(outs, 1.0, 1.0 / 3.0, out=gks, stream=stream)
             for _ in range(max(3, args.warmup)):
                 step()
             stream.synchronize()
@@ -692,7 +703,7 @@ def run_flux_workload(args, wl):
             # per step: long series (row max, prep, Gram, reduction) + the batch (5 descriptor
             # uploads, row max, prep, Gram, reduction) + one Green-Kubo integral per series
             # (counted in the ncu launch list, profiles/gram_band_kernel_polyphase_flux.md)
-            "gpu_launches": (4 + 9 + 1 + wl["nshort"]) * args.steps if args.method != "plain" else None,
+            "gpu_launches": (4 + 9 + 1) * args.steps if args.method != "plain" else None,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk.get("bf16_tflops", 1900.0),
                          "unit": "TFLOP/s", "frac": achieved / pk.get("bf16_tflops", 1900.0), "traffic": None,
                          "kernel": "gram_band_kernel (polyphase)",

@@ -169,6 +169,19 @@ int gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
                  double *d_running, void *stream);
 
 /*
+ * gk_integrate for count correlation functions of n values each in one
+ * launch: series j is read from d_c + j ldc and its running integral written
+ * to d_running + j ldr (offsets in doubles; ldc, ldr >= n).  Each series gets
+ * exactly the values a gk_integrate call on it would give.  The spans
+ * [d_c, d_c + (count-1) ldc + n) and [d_running, d_running + (count-1) ldr + n)
+ * may not overlap; both pointers 8-byte aligned.  count == 0 does nothing.
+ * Errors: TCORR_EINVAL (n < 1, count < 0, ldc or ldr < n, null pointer,
+ * overlapping spans), TCORR_EALIGN, TCORR_ECUDA.
+ */
+int gk_integrate_batch(const double *d_c, int64_t n, int64_t count, int64_t ldc, double dt,
+                       double prefactor, double *d_running, int64_t ldr, void *stream);
+
+/*
  * Einstein relation (Eq. 5): with t = tau dt, d_D[0] = b / (2 dim) where b is
  * the ordinary least-squares slope of d_msd[tau] against t over
  * tau in [lo, hi]; d_D[1] = d_msd[hi] / (2 dim hi dt) (the literal ratio).

@@ -378,6 +378,24 @@ int gk_integrate(const double *d_c, int64_t n, double dt, double prefactor, doub
     return TCORR_OK;
 }
 
+int gk_integrate_batch(const double *d_c, int64_t n, int64_t count, int64_t ldc, double dt, double prefactor,
+                       double *d_running, int64_t ldr, void *stream) {
+    if (n < 1 || count < 0 || ldc < n || ldr < n) return TCORR_EINVAL;
+    if (count == 0) return TCORR_OK;
+    if (!d_c || !d_running) return TCORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_c) & 7u) || (reinterpret_cast<uintptr_t>(d_running) & 7u))
+        return TCORR_EALIGN;
+    if (count > (INT64_MAX / 8 - n) / ldc || count > (INT64_MAX / 8 - n) / ldr) return TCORR_EINVAL;
+    // the spans [first series, end of the last) may not overlap
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(d_c), a1 = a0 + sizeof(double) * ((count - 1) * ldc + n);
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(d_running), b1 = b0 + sizeof(double) * ((count - 1) * ldr + n);
+    if (a0 < b1 && b0 < a1) return TCORR_EINVAL;
+    if (launch_gk_integrate_batch(d_c, n, count, ldc, dt, prefactor, d_running, ldr,
+                                  static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return TCORR_ECUDA;
+    return TCORR_OK;
+}
+
 int einstein_slope(const double *d_msd, int64_t n, double dt, int dim, int64_t lo, int64_t hi,
                    double *d_D, void *stream) {
     if (!d_msd || !d_D || dim < 1 || lo < 0 || hi <= lo || hi >= n || !(dt > 0.0))

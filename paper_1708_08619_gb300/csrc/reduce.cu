@@ -6,6 +6,7 @@
 //   gk_integrate -- running trapezoid integral of Eq. 4 (the quadrature loop
 //                   closing Algorithms 8 and 9, which the paper runs on the host);
 //   einstein     -- least-squares slope of the MSD and D = slope / (2d), Eq. 5.
+#include <algorithm>
 #include <cstring>
 
 #include "tcorr_internal.cuh"
@@ -138,9 +139,14 @@ __device__ __forceinline__ double block_excl_scan(double v, double *sh, double *
     return base + (inc - v);
 }
 
+// Batched launches: grid.y indexes the series; series y reads c + y ldc and
+// writes running + y ldr.
 __global__ void __launch_bounds__(GK_THREADS) gk_block_total_kernel(const double *c, int64_t n, double dt,
-                                                                     double *running) {
+                                                                     double *running, int64_t ldc,
+                                                                     int64_t ldr) {
     __shared__ double sh[GK_THREADS / 32];
+    c += static_cast<int64_t>(blockIdx.y) * ldc;
+    running += static_cast<int64_t>(blockIdx.y) * ldr;
     const int64_t k0 = 1 + static_cast<int64_t>(blockIdx.x) * GK_SPAN;
     const int64_t kb = k0 + static_cast<int64_t>(threadIdx.x) * GK_PER;
     double mine = 0.0;
@@ -152,8 +158,10 @@ __global__ void __launch_bounds__(GK_THREADS) gk_block_total_kernel(const double
 }
 
 // In place: running[1 + b SPAN] <- sum of the totals of blocks before b.
-__global__ void __launch_bounds__(GK_SCAN_THREADS) gk_scan_totals_kernel(double *running, int64_t nb) {
+__global__ void __launch_bounds__(GK_SCAN_THREADS) gk_scan_totals_kernel(double *running, int64_t nb,
+                                                                          int64_t ldr) {
     __shared__ double sh[GK_SCAN_THREADS / 32];
+    running += static_cast<int64_t>(blockIdx.y) * ldr;
     const int64_t per = ceil_div(nb, GK_SCAN_THREADS);
     const int64_t b0 = static_cast<int64_t>(threadIdx.x) * per, b1 = min(nb, b0 + per);
     double mine = 0.0;
@@ -171,9 +179,11 @@ __global__ void __launch_bounds__(GK_SCAN_THREADS) gk_scan_totals_kernel(double 
 // block re-sums the values before its span (0 for the first block).
 __global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *c, int64_t n, double dt,
                                                                    double prefactor, double *running,
-                                                                   int from_slot) {
+                                                                   int from_slot, int64_t ldc, int64_t ldr) {
     __shared__ double sh[GK_THREADS / 32];
     __shared__ double before_sh;
+    c += static_cast<int64_t>(blockIdx.y) * ldc;
+    running += static_cast<int64_t>(blockIdx.y) * ldr;
     const int64_t k0 = 1 + static_cast<int64_t>(blockIdx.x) * GK_SPAN;
     double before = 0.0;
     if (from_slot) {
@@ -181,8 +191,20 @@ __global__ void __launch_bounds__(GK_THREADS) gk_integrate_kernel(const double *
         __syncthreads();                    // the slot is read before this block writes its span
         before = before_sh;
     } else if (k0 > 1) {
-        double S = 0.0;
-        for (int64_t k = threadIdx.x; k < k0; k += GK_THREADS) S += c[k];
+        // eight interleaved partial sums keep eight loads in flight per thread
+        // (one running sum waits out a load latency per element); fixed order
+        double p[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int64_t k = threadIdx.x;
+        for (; k + 7 * GK_THREADS < k0; k += 8 * GK_THREADS) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) p[j] += c[k + j * GK_THREADS];
+        }
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {              // fewer than 8 strides remain
+            const int64_t kk = k + j * GK_THREADS;
+            if (kk < k0) p[j] += c[kk];
+        }
+        const double S = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
         double tot;
         block_excl_scan<GK_THREADS>(S, sh, &tot);
         before = dt * (2.0 * tot - c[0] - c[k0 - 1]) / 2.0;
@@ -329,18 +351,30 @@ cudaError_t upload_bytes(void *d_dst, const void *h_src, size_t nbytes, cudaStre
     return cudaSuccess;
 }
 
-cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
-                                double *d_running, cudaStream_t st) {
+cudaError_t launch_gk_integrate_batch(const double *d_c, int64_t n, int64_t count, int64_t ldc, double dt,
+                                      double prefactor, double *d_running, int64_t ldr, cudaStream_t st) {
     const int64_t blocks = n > 1 ? ceil_div(n - 1, GK_SPAN) : 1;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const unsigned g = static_cast<unsigned>(blocks);
     const bool three_pass = blocks > GK_RESUM_BLOCKS;
-    if (three_pass) {
-        gk_block_total_kernel<<<g, GK_THREADS, 0, st>>>(d_c, n, dt, d_running);
-        gk_scan_totals_kernel<<<1, GK_SCAN_THREADS, 0, st>>>(d_running, blocks);
+    constexpr int64_t kMaxY = 65535;           // grid.y limit: series in chunks
+    for (int64_t s0 = 0; s0 < count; s0 += kMaxY) {
+        const dim3 g(static_cast<unsigned>(blocks), static_cast<unsigned>(std::min(kMaxY, count - s0)));
+        const double *c = d_c + s0 * ldc;
+        double *r = d_running + s0 * ldr;
+        if (three_pass) {
+            gk_block_total_kernel<<<g, GK_THREADS, 0, st>>>(c, n, dt, r, ldc, ldr);
+            gk_scan_totals_kernel<<<dim3(1, g.y), GK_SCAN_THREADS, 0, st>>>(r, blocks, ldr);
+        }
+        gk_integrate_kernel<<<g, GK_THREADS, 0, st>>>(c, n, dt, prefactor, r, three_pass ? 1 : 0, ldc, ldr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    gk_integrate_kernel<<<g, GK_THREADS, 0, st>>>(d_c, n, dt, prefactor, d_running, three_pass ? 1 : 0);
-    return cudaGetLastError();
+    return cudaSuccess;
+}
+
+cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
+                                double *d_running, cudaStream_t st) {
+    return launch_gk_integrate_batch(d_c, n, 1, n, dt, prefactor, d_running, n, st);
 }
 
 cudaError_t launch_einstein(const double *d_msd, int64_t n, double dt, int dim, int64_t lo,

@@ -183,6 +183,9 @@ cudaError_t upload_bytes(void *d_dst, const void *h_src, size_t nbytes, cudaStre
 
 cudaError_t launch_gk_integrate(const double *d_c, int64_t n, double dt, double prefactor,
                                 double *d_running, cudaStream_t st);
+// count series at once: series j reads d_c + j ldc, writes d_running + j ldr.
+cudaError_t launch_gk_integrate_batch(const double *d_c, int64_t n, int64_t count, int64_t ldc, double dt,
+                                      double prefactor, double *d_running, int64_t ldr, cudaStream_t st);
 cudaError_t launch_einstein(const double *d_msd, int64_t n, double dt, int dim, int64_t lo,
                             int64_t hi, double *d_D, cudaStream_t st);
 

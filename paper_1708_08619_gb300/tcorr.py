@@ -55,6 +55,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tcorr_xcf.restype = ci
     lib.gk_integrate.argtypes = [vp, i64, dbl, dbl, vp, vp]
     lib.gk_integrate.restype = ci
+    lib.gk_integrate_batch.argtypes = [vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
+    lib.gk_integrate_batch.restype = ci
     lib.einstein_slope.argtypes = [vp, i64, dbl, ci, i64, i64, vp, vp]
     lib.einstein_slope.restype = ci
     lib.tcorr_batch_workspace_size.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci]
@@ -186,6 +188,27 @@ def gk_integrate(c, dt: float, prefactor: float = 1.0, out=None, stream=None):
     rc = load().gk_integrate(c.data_ptr(), c.numel(), dt, prefactor, out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "gk_integrate")
+    return out
+
+
+def gk_integrate_batch(c, dt: float, prefactor: float = 1.0, out=None, stream=None):
+    """gk_integrate of every row of a [count][n] float64 CUDA tensor, one launch.
+
+    Rows may be padded (row stride >= n, unit column stride); out gets the
+    same shape (a new contiguous tensor by default).
+    """
+    torch = _torch()
+    if not c.is_cuda or c.dtype != torch.float64 or c.dim() != 2 or c.stride(1) != 1:
+        raise TypeError("c must be a [count][n] float64 CUDA tensor with unit column stride")
+    if out is None:
+        out = torch.empty(c.shape, dtype=torch.float64, device=c.device)
+    if tuple(out.shape) != tuple(c.shape) or out.dtype != torch.float64 or out.stride(1) != 1:
+        raise TypeError("out must be a float64 tensor shaped like c with unit column stride")
+    count, n = c.shape
+    rc = load().gk_integrate_batch(c.data_ptr(), n, count, c.stride(0) if count > 1 else n, dt, prefactor,
+                                   out.data_ptr(), out.stride(0) if count > 1 else n, _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "gk_integrate_batch")
     return out
 
 

@@ -99,6 +99,16 @@ def test_gk_and_einstein_validation(lib):
     assert lib.gk_integrate(FAKE_X, 0, 1.0, 1.0, FAKE_OUT, None) == 1
     assert lib.gk_integrate(FAKE_X + 4, 10, 1.0, 1.0, FAKE_OUT, None) == 2
     assert lib.gk_integrate(FAKE_X, 10, 1.0, 1.0, FAKE_X + 8, None) == 1   # overlap
+    gb = lib.gk_integrate_batch
+    assert gb(FAKE_X, 10, 0, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 0          # nothing to do
+    assert gb(None, 10, 2, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 1
+    assert gb(FAKE_X, 0, 2, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 1
+    assert gb(FAKE_X, 10, -1, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 1
+    assert gb(FAKE_X, 10, 2, 9, 1.0, 1.0, FAKE_OUT, 10, None) == 1           # ldc < n
+    assert gb(FAKE_X, 10, 2, 10, 1.0, 1.0, FAKE_OUT, 9, None) == 1           # ldr < n
+    assert gb(FAKE_X + 4, 10, 2, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 2
+    assert gb(FAKE_X, 10, 3, 10, 1.0, 1.0, FAKE_X + 8 * 25, 10, None) == 1   # spans overlap
+    assert gb(FAKE_X, 10, 1 << 60, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 1    # span overflows
     D = FAKE_OUT
     assert lib.einstein_slope(FAKE_X, 10, 1.0, 3, 5, 5, D, None) == 1     # hi <= lo
     assert lib.einstein_slope(FAKE_X, 10, 1.0, 3, 2, 10, D, None) == 1    # hi >= n

@@ -98,6 +98,28 @@ def test_gk_integrate_and_einstein(T):
     assert abs(got2[0] / want2[0] - 1) < 1e-12
 
 
+def test_gk_integrate_batch(T):
+    rng = np.random.default_rng(10)
+    # single-launch and three-pass sizes; padded rows; a grid taller than 65535 series
+    for n, count, pad in ((1, 3, 0), (20001, 65, 0), (5001, 7, 13), (65538, 3, 5), (3, 70000, 1)):
+        c = rng.normal(size=(count, n + pad))
+        cd = dev(c)[:, :n]
+        got = T.gk_integrate_batch(cd, 0.25, 3.5).cpu().numpy()
+        for j in {0, count // 2, count - 1}:
+            want = oracle.gk_integrate(c[j, :n], 0.25, 3.5)
+            assert np.allclose(got[j], want, rtol=1e-12, atol=1e-12 * np.abs(want).max(initial=1.0)), (n, j)
+            single = T.gk_integrate(cd[j].contiguous(), 0.25, 3.5).cpu().numpy()
+            assert np.array_equal(got[j], single), (n, j)      # same arithmetic as one call
+    # a padded output
+    c = rng.normal(size=(4, 3000))
+    out = torch.full((4, 3010), 7.0, dtype=torch.float64, device="cuda")
+    T.gk_integrate_batch(dev(c), 1.0, 1.0, out=out[:, :3000])
+    o = out.cpu().numpy()
+    assert np.all(o[:, 3000:] == 7.0)
+    assert np.allclose(o[2, :3000], oracle.gk_integrate(c[2], 1.0, 1.0), rtol=1e-12, atol=1e-9)
+    assert T.tcorr_status_poll() == 0
+
+
 def test_batch_matches_single_calls(T):
     rng = np.random.default_rng(21)
     items, refs = [], []
