@@ -225,10 +225,10 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
  * frames are the origins it owns, the rest is the tau_max halo of partner
  * frames.  Each window runs the tensor-core band kernel (or the plain
  * kernel) restricted to its own origins and adds the per-lag numerators into
- * d_out; one last kernel divides by N n_o(tau) of the whole trajectory.  Two
- * window buffers alternate: the halo is copied from the previous window on
+ * d_out; one last kernel divides by N n_o(tau) of the whole trajectory.  Three
+ * window buffers rotate: the halo is copied from the previous window on
  * the device and only the C new frames come from the host, on a second
- * stream that overlaps the previous window's kernels.  Polyphase (small K)
+ * stream that overlaps the earlier windows' kernels.  Polyphase (small K)
  * is not used in this mode; the band form handles every K.
  * h_x   : [T][N][3] float32 in host memory, 4-byte aligned.  Pinned memory
  *         (cudaHostAlloc / cudaHostRegister) lets the copies overlap the
@@ -236,7 +236,7 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
  *         h_x must stay valid and unchanged until `stream` has finished.
  * d_out : tau_max+1 doubles on the device, 8-byte aligned (overwritten).
  * d_ws  : device workspace of ws_bytes >= tcorr_stream_workspace_size(...),
- *         256-byte aligned: two window buffers of min(T, C + tau_max) frames
+ *         256-byte aligned: min(3, windows) window buffers of min(T, C + tau_max) frames
  *         plus the engine's workspace for one window.
  * The call enqueues work on `stream` and on a stream of its own, joined back
  * to `stream` through events; it cannot be captured in a CUDA graph.

@@ -13,11 +13,14 @@
 // at C and its per-lag numerators added into d_out; one last kernel divides
 // by N n_o(tau) of the whole trajectory.
 //
-// Copies: two window buffers alternate.  Window c's halo (its first tau_max
+// Copies: three window buffers rotate.  Window c's halo (its first tau_max
 // frames) is the tail of window c-1 and is copied device to device; only the
 // new frames cross from the host, so each frame crosses once.  Copies run
-// on a second stream and overlap the previous window's kernels; events order
-// buffer reuse.
+// on a second stream and overlap the earlier windows' kernels; events order
+// buffer reuse.  With two buffers the copy of window c waited for window
+// c-2's kernels, so whenever the window kernels queued behind other work on
+// the device (an in-core call on another stream) the host link went idle;
+// the third buffer lets the copies run one window further ahead.
 #include <cstdint>
 #include <vector>
 
@@ -26,6 +29,8 @@
 namespace tcorr {
 
 namespace {
+
+constexpr int NBUF = 3;             // window buffers in rotation
 
 // Origins per window when the caller passes 0: four halos' worth, at least
 // 4096 frames, whole 128-origin row tiles.
@@ -40,7 +45,8 @@ struct StreamPlan {
     int method;                 // resolved (never TCORR_AUTO)
     int64_t K, C, W, n_win;     // K = 3N; origins per window; largest window; windows
     std::vector<int64_t> start; // first frame of each window (multiples of s), then T
-    size_t off_buf[2], off_engine, engine_bytes, total;
+    int nbuf;                   // window buffers in use: min(NBUF, windows)
+    size_t off_buf[NBUF], off_engine, engine_bytes, total;
 };
 
 // Windows of C origin frames, except that the last stretch is cut so that the
@@ -105,10 +111,10 @@ bool make_stream_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int meth
         if (need > P->engine_bytes) P->engine_bytes = need;
     }
     const size_t buf = align256(static_cast<size_t>(P->W) * static_cast<size_t>(P->K) * sizeof(float));
-    P->off_buf[0] = 0;
-    P->off_buf[1] = buf;
-    P->off_engine = 2 * buf;
-    P->total = 2 * buf + align256(P->engine_bytes);
+    P->nbuf = static_cast<int>(P->n_win < NBUF ? P->n_win : NBUF);
+    for (int i = 0; i < NBUF; ++i) P->off_buf[i] = static_cast<size_t>(i < P->nbuf ? i : 0) * buf;
+    P->off_engine = static_cast<size_t>(P->nbuf) * buf;
+    P->total = static_cast<size_t>(P->nbuf) * buf + align256(P->engine_bytes);
     return true;
 }
 
@@ -116,17 +122,23 @@ bool make_stream_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s, int meth
 // still queued is allowed (CUDA releases them when that work completes).
 struct StreamRes {
     cudaStream_t side = nullptr;
-    cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, copied[NBUF] = {}, freed[NBUF] = {};
     ~StreamRes() {
-        for (cudaEvent_t e : {start, copied[0], copied[1], freed[0], freed[1]})
-            if (e) cudaEventDestroy(e);
+        if (start) cudaEventDestroy(start);
+        for (int i = 0; i < NBUF; ++i) {
+            if (copied[i]) cudaEventDestroy(copied[i]);
+            if (freed[i]) cudaEventDestroy(freed[i]);
+        }
         if (side) cudaStreamDestroy(side);
     }
     cudaError_t init() {
         cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
-        for (cudaEvent_t *p : {&start, &copied[0], &copied[1], &freed[0], &freed[1]})
-            if ((e = cudaEventCreateWithFlags(p, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess) return e;
+        for (int i = 0; i < NBUF; ++i)
+            if ((e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming)) != cudaSuccess)
+                return e;
         return cudaSuccess;
     }
 };
@@ -147,7 +159,8 @@ int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max
     cudaError_t e = R.init();
     if (e != cudaSuccess) return cuda_fail(e, "stream resources");
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
-    float *buf[2] = {reinterpret_cast<float *>(ws + P.off_buf[0]), reinterpret_cast<float *>(ws + P.off_buf[1])};
+    float *buf[NBUF];
+    for (int i = 0; i < NBUF; ++i) buf[i] = reinterpret_cast<float *>(ws + P.off_buf[i]);
     const size_t row = static_cast<size_t>(P.K) * sizeof(float);
     if ((e = cudaMemsetAsync(d_out, 0, sizeof(double) * static_cast<size_t>(tau_max + 1), st)) != cudaSuccess)
         return cuda_fail(e, "output reset");
@@ -155,16 +168,16 @@ int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max
     if ((e = cudaEventRecord(R.start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(R.side, R.start, 0)) != cudaSuccess)
         return cuda_fail(e, "stream fork");
     for (int64_t c = 0; c < P.n_win; ++c) {
-        const int b = static_cast<int>(c & 1);
+        const int b = static_cast<int>(c % P.nbuf), pb = static_cast<int>((c + P.nbuf - 1) % P.nbuf);
         const int64_t t0 = P.start[c], Wc = window_frames(P, T, tau_max, c);
-        if (c >= 2 && (e = cudaStreamWaitEvent(R.side, R.freed[b], 0)) != cudaSuccess)
+        if (c >= P.nbuf && (e = cudaStreamWaitEvent(R.side, R.freed[b], 0)) != cudaSuccess)
             return cuda_fail(e, "buffer reuse wait");
         int64_t have = 0;
         if (c > 0) {        // halo: frames [t0, t0 + h) follow the previous window's origin frames
             have = tau_max < Wc ? tau_max : Wc;
             const int64_t prev_len = t0 - P.start[c - 1];
             if (have > 0 &&
-                (e = cudaMemcpyAsync(buf[b], buf[1 - b] + static_cast<size_t>(prev_len) * P.K, have * row,
+                (e = cudaMemcpyAsync(buf[b], buf[pb] + static_cast<size_t>(prev_len) * P.K, have * row,
                                      cudaMemcpyDeviceToDevice, R.side)) != cudaSuccess)
                 return cuda_fail(e, "halo copy");
         }

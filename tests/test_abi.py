@@ -159,13 +159,14 @@ def test_stream_misaligned_and_workspace(lib):
     assert call_msd_stream(lib, chunk=32, ws_bytes=need - 1) == 4
 
 
-def test_stream_workspace_holds_two_windows(lib):
+def test_stream_workspace_holds_three_windows(lib):
     T, N, tm = 5000, 64, 300
     small = lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 512)
     big = lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 2048)
-    assert 2 * (512 + tm) * N * 3 * 4 <= small < big
-    # a chunk covering the whole trajectory is one window of T frames
-    assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 10 ** 9) >= 2 * T * N * 3 * 4
+    assert 3 * (512 + tm) * N * 3 * 4 <= small < big
+    # a chunk covering the whole trajectory is one window (one buffer) of T frames
+    whole = lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, 10 ** 9)
+    assert T * N * 3 * 4 <= whole < 2 * T * N * 3 * 4 + lib.tcorr_workspace_size(T, N, tm, 1, 0)
     assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, -1) == 0
 
 
