@@ -122,16 +122,26 @@ def _alloc_ws(nbytes: int, device):
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
+def _held_by(t, stream):
+    """A tensor allocated here for a call on ``stream``: torch's caching allocator
+    allocated it on the current stream, so it is marked as used by ``stream`` too;
+    otherwise its memory could go to another allocation as soon as the binding
+    drops it, while the call's kernels still run."""
+    if t is not None and stream is not None:
+        t.record_stream(stream)
+    return t
+
+
 def _corr(fname: str, x, tau_max: int, stride: int, method, out, ws, stream):
     torch = _torch()
     _check_traj(x)
     T, N, _ = x.shape
     m = _method(method)
     if out is None:
-        out = torch.empty(tau_max + 1, dtype=torch.float64, device=x.device)
+        out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=x.device), stream)
     need = tcorr_workspace_size(T, N, tau_max, stride, m)
     if ws is None:
-        ws = _alloc_ws(need, x.device)
+        ws = _held_by(_alloc_ws(need, x.device), stream)
     ws_ptr = ws.data_ptr() if ws is not None else None
     ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = getattr(load(), fname)(x.data_ptr(), T, N, tau_max, stride, m, out.data_ptr(),
@@ -165,10 +175,10 @@ def tcorr_xcf(a, b, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=Non
     T, N, _ = a.shape
     m = _method(method)
     if out is None:
-        out = torch.empty(tau_max + 1, dtype=torch.float64, device=a.device)
+        out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=a.device), stream)
     need = tcorr_xcf_workspace_size(T, N, tau_max, stride, m)
     if ws is None:
-        ws = _alloc_ws(need, a.device)
+        ws = _held_by(_alloc_ws(need, a.device), stream)
     ws_ptr = ws.data_ptr() if ws is not None else None
     ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = load().tcorr_xcf(a.data_ptr(), b.data_ptr(), T, N, tau_max, stride, m, out.data_ptr(), ws_ptr, ws_bytes,
@@ -184,7 +194,7 @@ def gk_integrate(c, dt: float, prefactor: float = 1.0, out=None, stream=None):
     if not c.is_cuda or c.dtype != torch.float64 or not c.is_contiguous():
         raise TypeError("c must be a contiguous float64 CUDA tensor")
     if out is None:
-        out = torch.empty_like(c)
+        out = _held_by(torch.empty_like(c), stream)
     rc = load().gk_integrate(c.data_ptr(), c.numel(), dt, prefactor, out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "gk_integrate")
@@ -201,7 +211,7 @@ def gk_integrate_batch(c, dt: float, prefactor: float = 1.0, out=None, stream=No
     if not c.is_cuda or c.dtype != torch.float64 or c.dim() != 2 or c.stride(1) != 1:
         raise TypeError("c must be a [count][n] float64 CUDA tensor with unit column stride")
     if out is None:
-        out = torch.empty(c.shape, dtype=torch.float64, device=c.device)
+        out = _held_by(torch.empty(c.shape, dtype=torch.float64, device=c.device), stream)
     if tuple(out.shape) != tuple(c.shape) or out.dtype != torch.float64 or out.stride(1) != 1:
         raise TypeError("out must be a float64 tensor shaped like c with unit column stride")
     count, n = c.shape
@@ -224,7 +234,7 @@ def einstein_slope(msd, dt: float, dim: int = 3, lo: int | None = None, hi: int 
     if lo is None:
         lo = -(-(2 * hi) // 10)
     if out is None:
-        out = torch.empty(2, dtype=torch.float64, device=msd.device)
+        out = _held_by(torch.empty(2, dtype=torch.float64, device=msd.device), stream)
     rc = load().einstein_slope(msd.data_ptr(), n, dt, dim, lo, hi, out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "einstein_slope")
@@ -252,7 +262,7 @@ def tcorr_batch(instances, method=AUTO, ws=None, stream=None, device=None):
     m = _method(method)
     need = tcorr_batch_workspace_size(instances, m)
     if ws is None:
-        ws = _alloc_ws(need, device or torch.device("cuda"))
+        ws = _held_by(_alloc_ws(need, device or torch.device("cuda")), stream)
     ws_ptr = ws.data_ptr() if ws is not None else None
     ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = load().tcorr_batch(instances, len(instances), m, ws_ptr, ws_bytes, _stream_ptr(stream))
@@ -275,10 +285,10 @@ def _corr_stream(fname: str, x, tau_max: int, stride: int, method, chunk_frames:
     m = _method(method)
     device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     if out is None:
-        out = torch.empty(tau_max + 1, dtype=torch.float64, device=device)
+        out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=device), stream)
     need = tcorr_stream_workspace_size(T, N, tau_max, stride, m, chunk_frames)
     if ws is None:
-        ws = _alloc_ws(need, device)
+        ws = _held_by(_alloc_ws(need, device), stream)
     ws_ptr = ws.data_ptr() if ws is not None else None
     ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     rc = getattr(load(), fname)(x.data_ptr(), T, N, tau_max, stride, m, chunk_frames, out.data_ptr(),
@@ -307,7 +317,7 @@ def tcorr_plain_static(kind: int, x, tau_max: int, stride: int = 1, out=None, st
     torch = _torch()
     _check_traj(x)
     if out is None:
-        out = torch.empty(tau_max + 1, dtype=torch.float64, device=x.device)
+        out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=x.device), stream)
     rc = load().tcorr_plain_static(kind, x.data_ptr(), x.shape[0], x.shape[1], tau_max, stride,
                                    out.data_ptr(), _stream_ptr(stream))
     if rc != 0:

@@ -141,3 +141,37 @@ def test_stream_small_last_window_large_k(T, method):
     lags = np.array([0, 1, 2, 127, 128, 500, 999, 1000])
     ref = oracle.msd(xh, stride=1, lags=lags)
     check_vs_oracle(0, got[lags], ref, method)
+
+
+def test_stream_concurrent_with_incore_call_on_another_stream(T):
+    """An in-core MSD on one stream while a streamed VACF (more windows than
+    window buffers, so buffers are reused) runs on another, the streamed
+    call's copies held until the positions' copy has landed: both results
+    match the oracle, and the streamed one equals the same call run alone."""
+    Tn, N, tm, chunk = 2600, 96, 300, 256
+    xh, vh = traj(0, Tn, N, 71), traj(1, Tn, N, 72)
+    alone = streamed(T, 1, vh, tm, 1, "fp16x3", chunk)
+    xhp, vhp = host(xh, True), host(vh, True)
+    xd = torch.empty((Tn, N, 3), dtype=torch.float32, device="cuda")
+    sa, sb, sc = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    landed = torch.cuda.Event()
+    with torch.cuda.stream(sc):
+        xd.copy_(xhp, non_blocking=True)
+        landed.record(sc)
+    sa.wait_event(landed)
+    sb.wait_event(landed)
+    m = T.tcorr_msd(xd, tm, 1, "fp16x3", stream=sa)
+    c = T.tcorr_acf_stream(vhp, tm, 1, "fp16x3", chunk_frames=chunk, stream=sb)
+    # the bindings allocated both workspaces on the current stream and dropped them; fresh
+    # allocations there, filled at once, must not get that memory while sa / sb still use it
+    junk = [torch.full((T.tcorr_workspace_size(Tn, N, tm, 1, "fp16x3"),), 255, dtype=torch.uint8, device="cuda"),
+            torch.full((T.tcorr_stream_workspace_size(Tn, N, tm, 1, "fp16x3", chunk),), 255, dtype=torch.uint8,
+                       device="cuda")]
+    torch.cuda.synchronize()
+    del junk
+    lags = np.arange(tm + 1)
+    check_vs_oracle(0, m.cpu().numpy(), oracle.msd(xh, stride=1, lags=lags), "fp16x3")
+    cc = c.cpu().numpy()
+    check_vs_oracle(1, cc, oracle.acf(vh, stride=1, lags=lags), "fp16x3")
+    assert np.array_equal(cc, alone)
+    assert T.tcorr_status_poll() == 0
