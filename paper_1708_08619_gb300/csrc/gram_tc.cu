@@ -891,24 +891,32 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
     if (ke - kb <= NCH * STEP) {
         float x[NCH][8];
         float mx = 0.f;
-        // MSD: the reference frame's values are loaded with their rows, half the chunks at a
-        // time, so that the loads in flight fit the registers
+        // every chunk of the row is requested first (the loads from DRAM all in flight at
+        // once); the MSD's reference-frame values (L2-resident) follow half the chunks at a
+        // time, so that the registers hold the row plus half a row of references
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int64_t k0 = kb + c * STEP + static_cast<int64_t>(tid) * 8;
+            if (k0 < ke) {
+                load8<1, VEC>(row, X, k0, Klive, x[c]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[c][i] = 0.f;
+            }
+        }
         constexpr int NH = KIND == 0 ? NCH / 2 : NCH;
 #pragma unroll
         for (int h = 0; h < NCH / NH; ++h) {
             float r[KIND == 0 ? NH : 1][8];
+            if (KIND == 0) {
 #pragma unroll
-            for (int cc = 0; cc < NH; ++cc) {
-                const int c = h * NH + cc;
-                const int64_t k0 = kb + c * STEP + static_cast<int64_t>(tid) * 8;
-                if (k0 < ke) {
-                    load8<1, VEC>(row, X, k0, Klive, x[c]);
-                    if (KIND == 0) load8<1, VEC>(q.ref, q.ref, k0, Klive, r[cc]);
-                } else {
+                for (int cc = 0; cc < NH; ++cc) {
+                    const int64_t k0 = kb + (h * NH + cc) * STEP + static_cast<int64_t>(tid) * 8;
+                    if (k0 < ke) {
+                        load8<1, VEC>(q.ref, q.ref, k0, Klive, r[cc]);
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        x[c][i] = 0.f;
-                        if (KIND == 0) r[cc][i] = 0.f;
+                        for (int i = 0; i < 8; ++i) r[cc][i] = 0.f;
                     }
                 }
             }
