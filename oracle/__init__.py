@@ -6,8 +6,9 @@ links or calls anything here, and nothing here imports the CUDA library.
 
 The arithmetic lives in ``tcorr_oracle.c`` (plain FP64 loops following
 Eq. 5 / Algorithm 10 for the MSD, Eq. 4 / Algorithm 8 for the
-autocorrelation and its running Green-Kubo integral, and the same loop nest
-with the later factor taken from a second signal for the cross-correlation).  This module compiles it
+autocorrelation and its running Green-Kubo integral, the same loop nest
+with the later factor taken from a second signal for the cross-correlation,
+and the weighted atom sum that forms a collective signal).  This module compiles it
 with gcc (no FMA contraction, no fast-math, so x86 and Arm give the same bits)
 and marshals numpy arrays through ctypes.
 
@@ -56,6 +57,8 @@ def load_library(path: str) -> ctypes.CDLL:
     lib.oracle_corr.restype = ctypes.c_int
     lib.oracle_xcorr.argtypes = [vp, vp, i64, i64, i64, vp, i64, vp, ctypes.c_int]
     lib.oracle_xcorr.restype = ctypes.c_int
+    lib.oracle_collective.argtypes = [vp, vp, i64, i64, i64, vp]
+    lib.oracle_collective.restype = ctypes.c_int
     lib.oracle_gk_integrate.argtypes = [vp, i64, dbl, dbl, vp]
     lib.oracle_gk_integrate.restype = ctypes.c_int
     lib.oracle_einstein.argtypes = [vp, i64, dbl, ctypes.c_int, i64, i64, vp, vp]
@@ -126,6 +129,23 @@ def xcf(a, b, tau_max=None, stride=1, lags=None, nthreads=None, lib=None) -> np.
                           lags.shape[0], out.ctypes.data, nthreads or default_threads())
     if rc != 0:
         raise ValueError(f"oracle_xcorr failed with code {rc}")
+    return out
+
+
+def collective(x, w=None, ref_frame: int = -1, lib=None) -> np.ndarray:
+    """J[t][c] = sum_i w_i (x[t][i][c] - x[ref][i][c]) in FP64 ([T][3]); ref_frame -1: no reference."""
+    lib = lib or _get_lib()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    T, N = x.shape[0], x.shape[1]
+    wp = None
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.shape != (N,):
+            raise ValueError("w must hold one weight per atom")
+        wp = w.ctypes.data
+    out = np.zeros((T, 3), dtype=np.float64)
+    if lib.oracle_collective(x.ctypes.data, wp, T, N, ref_frame, out.ctypes.data) != 0:
+        raise ValueError("oracle_collective: bad arguments")
     return out
 
 

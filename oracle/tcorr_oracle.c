@@ -43,6 +43,9 @@
  *   MSD(tau) against t = tau dt over [lo, hi], D = b / (2 d); and the literal
  *   ratio MSD(hi) / (2 d hi dt).
  *
+ *   Collective signal (for collective transport coefficients): the weighted
+ *   sum over atoms J[t] = sum_i w_i (x[t][i] - x[ref][i]).
+ *
  * Layout of the trajectory: x[T][N][3] float32, row-major (frame-major),
  * the linear array of Sec. 2.3.
  *
@@ -209,6 +212,33 @@ int oracle_gk_integrate(const double *c, int64_t n, double dt, double prefactor,
     for (int64_t k = 1; k < n; ++k) {
         I += dt * (c[k - 1] + c[k]) / 2.0;
         running[k] = prefactor * I;
+    }
+    return 0;
+}
+
+/*
+ * Collective signal: the system-wide sum whose time correlation gives a
+ * collective transport coefficient (Eq. 4 with a collective flux, as the
+ * viscosity example correlates the pressure tensor of the whole box; the
+ * Einstein-Helfand form takes the MSD of the summed, weighted positions):
+ *   J[t][c] = sum_i w[i] (x[t][i][c] - x[ref][i][c])   for 0 <= ref < T,
+ *   J[t][c] = sum_i w[i] x[t][i][c]                     for ref = -1,
+ * in FP64 from the FP32 inputs promoted exactly, atoms in increasing order;
+ * w == NULL means unit weights.  J: T x 3 doubles.
+ */
+int oracle_collective(const float *x, const float *w, int64_t T, int64_t N, int64_t ref,
+                      double *J) {
+    if (!x || !J || T < 1 || N < 1 || ref < -1 || ref >= T) return -1;
+    for (int64_t t = 0; t < T; ++t) {
+        for (int c = 0; c < 3; ++c) {
+            double sum = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double v = (double)x[(t * N + i) * 3 + c];
+                if (ref >= 0) v -= (double)x[(ref * N + i) * 3 + c];
+                sum += (w ? (double)w[i] : 1.0) * v;
+            }
+            J[t * 3 + c] = sum;
+        }
     }
     return 0;
 }

@@ -15,7 +15,9 @@ definitions and plain mathematics fix:
   the split of stride-1 origins into two stride-2 sets;
 * statistics: random walk (E[MSD] = 3 sigma^2 tau), Ornstein-Uhlenbeck
   (C(tau)/C(0) = phi^tau within Bartlett errors), and Einstein D = Green-Kubo D
-  for positions integrated from OU velocities.
+  for positions integrated from OU velocities;
+* the collective (weighted atom-sum) signal: one-hot selection, linearity,
+  shift invariance, the ballistic closed form and its Einstein-Helfand MSD.
 
 The same functions run against planted-mistake copies of the oracle in
 ``test_oracle_mutants.py``; each copy must fail at least one of them.
@@ -359,9 +361,55 @@ def pin_xcf_closed_forms(lib):
         raise AssertionError("xcf(A, A) differs from acf(A)")
 
 
+# ----------------------------------------------------------------- collective signal
+
+def pin_collective(lib):
+    """The weighted atom sum J[t] = sum_i w_i (x[t][i] - x[ref][i]) on dyadic data
+    (every product and partial sum exact in FP64, so each check is bit for bit):
+    one-hot weights select one atom; J is linear in the weights; with a reference
+    frame J does not change when each atom is shifted by a constant; unit weights
+    (no weight array) are the plain atom sum; and a constant-velocity system gives
+    J(t) = (sum_i w_i v_i)(t - ref), whose MSD is |sum_i w_i v_i|^2 tau^2 (the
+    Einstein-Helfand MSD of a ballistic system)."""
+    rng = np.random.default_rng(41)
+    T, N = 40, 7
+    x = (rng.integers(-4096, 4096, size=(T, N, 3)) / 1024.0).astype(np.float32)
+    w1 = (rng.integers(-16, 16, size=N) / 8.0).astype(np.float32)
+    w2 = (rng.integers(-16, 16, size=N) / 8.0).astype(np.float32)
+    for ref in (-1, 0, 17, T - 1):
+        for j in (0, 3, N - 1):
+            e = np.zeros(N, dtype=np.float32)
+            e[j] = 1.0
+            want = x[:, j, :].astype(np.float64) - (x[ref, j].astype(np.float64) if ref >= 0 else 0.0)
+            if not np.array_equal(oracle.collective(x, e, ref, lib=lib), want):
+                raise AssertionError(f"collective one-hot atom {j} ref {ref}")
+        lin = oracle.collective(x, w1, ref, lib=lib) + oracle.collective(x, w2, ref, lib=lib)
+        if not np.array_equal(oracle.collective(x, w1 + w2, ref, lib=lib), lin):
+            raise AssertionError(f"collective not linear in the weights (ref {ref})")
+        plain = (x.astype(np.float64) - (x[ref].astype(np.float64) if ref >= 0 else 0.0)).sum(axis=1)
+        if not np.array_equal(oracle.collective(x, None, ref, lib=lib), plain):
+            raise AssertionError(f"collective with unit weights (ref {ref})")
+    shift = (rng.integers(-64, 64, size=(1, N, 3)) / 4.0).astype(np.float32)
+    for ref in (0, 9):
+        if not np.array_equal(oracle.collective(x + shift, w1, ref, lib=lib), oracle.collective(x, w1, ref, lib=lib)):
+            raise AssertionError(f"collective with a reference frame changed under per-atom shifts (ref {ref})")
+    x0 = (rng.integers(-64, 64, size=(N, 3)) / 8.0).astype(np.float32)
+    v = (rng.integers(-64, 64, size=(N, 3)) / 256.0).astype(np.float32)
+    t = np.arange(T, dtype=np.float64)
+    xc = (x0[None].astype(np.float64) + v[None].astype(np.float64) * t[:, None, None]).astype(np.float32)
+    wv = (w1[:, None].astype(np.float64) * v.astype(np.float64)).sum(axis=0)
+    for ref in (0, 11):
+        J = oracle.collective(xc, w1, ref, lib=lib)
+        if not np.array_equal(J, wv[None] * (t - ref)[:, None]):
+            raise AssertionError(f"collective constant-velocity closed form (ref {ref})")
+        m = oracle.msd(J.astype(np.float32)[:, None, :], T - 1, lib=lib)
+        _close(m, float((wv ** 2).sum()) * t ** 2, 1e-15, what=f"Einstein-Helfand MSD, ballistic (ref {ref})")
+
+
 ALL_PINS = [
     pin_hand_worked, pin_brute_force, pin_lag_subset, pin_fft, pin_constant_velocity,
     pin_zero_lag, pin_single_origin, pin_invariants, pin_stride_split,
     pin_gk_closed_forms, pin_einstein_exact, pin_random_walk, pin_ou,
     pin_einstein_vs_green_kubo, pin_xcf_brute_force, pin_xcf_fft, pin_xcf_closed_forms,
+    pin_collective,
 ]

@@ -34,6 +34,11 @@ MUTANTS = [
     ("xcf_second_signal_ignored", "later[3 * t + c] = (double)J->y[", "later[3 * t + c] = (double)J->x[", 0),
     ("xcf_time_roles_swapped", "const double *p = traj + 3 * t0;\n                const double *q = later + 3 * (t0 + tau);",
      "const double *p = later + 3 * t0;\n                const double *q = traj + 3 * (t0 + tau);", 0),
+    ("collective_ref_ignored", "if (ref >= 0) v -= (double)x[(ref * N + i) * 3 + c];", "", 0),
+    ("collective_weight_ignored", "sum += (w ? (double)w[i] : 1.0) * v;", "sum += v;", 0),
+    ("collective_ref_wrong_atom", "v -= (double)x[(ref * N + i) * 3 + c];", "v -= (double)x[(ref * N) * 3 + c];", 0),
+    ("collective_component_fixed", "double v = (double)x[(t * N + i) * 3 + c];",
+     "double v = (double)x[(t * N + i) * 3];", 0),
 ]
 
 
