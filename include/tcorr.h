@@ -182,6 +182,31 @@ int gk_integrate_batch(const double *d_c, int64_t n, int64_t count, int64_t ldc,
                        double prefactor, double *d_running, int64_t ldr, void *stream);
 
 /*
+ * Collective signal of a trajectory, the input of collective transport
+ * quantities (Eq. 4 with a collective flux, as the viscosity example
+ * correlates the pressure tensor of the whole box):
+ *   d_out[t][c] = sum_i w_i (x[t][i][c] - x[ref_frame][i][c])  (0 <= ref_frame < T)
+ *   d_out[t][c] = sum_i w_i  x[t][i][c]                        (ref_frame = -1)
+ * d_out is a [T][1][3] float32 trajectory of one "atom", ready for
+ * tcorr_msd / tcorr_acf / tcorr_xcf with N = 1: with charges q_i as weights,
+ * the MSD of the summed charged positions (Einstein-Helfand; take a reference
+ * frame, which the MSD does not see, to keep the FP32 values small) or the
+ * autocorrelation of the charge current (ref_frame = -1); with 0/1 weights,
+ * the signal of an atom selection or species, e.g. for the velocity
+ * cross-correlation of two species through tcorr_xcf.
+ * d_x: [T][N][3] float32 (device, 4-byte aligned); d_w: N float32 weights
+ * (device, 4-byte aligned) or NULL for unit weights; d_out: 3T floats, not
+ * overlapping d_x or d_w.  Arithmetic: products and sums carried with their
+ * rounding errors in FP32 (compensated dot product), combined per frame in
+ * FP64 in a fixed order; with a reference frame its totals, formed the same
+ * way, are subtracted in FP64; one rounding to FP32 (deterministic).
+ * Errors: TCORR_EINVAL (null pointer, T < 1, N < 1, ref_frame outside
+ * [-1, T-1], overlapping output), TCORR_EALIGN, TCORR_ECUDA.
+ */
+int tcorr_collective(const float *d_x, const float *d_w, int64_t T, int64_t N, int64_t ref_frame,
+                     float *d_out, void *stream);
+
+/*
  * Einstein relation (Eq. 5): with t = tau dt, d_D[0] = b / (2 dim) where b is
  * the ordinary least-squares slope of d_msd[tau] against t over
  * tau in [lo, hi]; d_D[1] = d_msd[hi] / (2 dim hi dt) (the literal ratio).

@@ -57,6 +57,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gk_integrate.restype = ci
     lib.gk_integrate_batch.argtypes = [vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
     lib.gk_integrate_batch.restype = ci
+    lib.tcorr_collective.argtypes = [vp, vp, i64, i64, i64, vp, vp]
+    lib.tcorr_collective.restype = ci
     lib.einstein_slope.argtypes = [vp, i64, dbl, ci, i64, i64, vp, vp]
     lib.einstein_slope.restype = ci
     lib.tcorr_batch_workspace_size.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci]
@@ -219,6 +221,23 @@ def gk_integrate_batch(c, dt: float, prefactor: float = 1.0, out=None, stream=No
                                    out.data_ptr(), out.stride(0) if count > 1 else n, _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "gk_integrate_batch")
+    return out
+
+
+def tcorr_collective(x, w=None, ref_frame: int = -1, out=None, stream=None):
+    """sum_i w_i (x[t][i] - x[ref_frame][i]) per frame as a [T][1][3] float32 trajectory
+    (ref_frame -1: no reference; w None: unit weights)."""
+    torch = _torch()
+    _check_traj(x)
+    T, N, _ = x.shape
+    if w is not None and (not w.is_cuda or w.dtype != torch.float32 or w.numel() != N or not w.is_contiguous()):
+        raise TypeError("w must be a contiguous float32 CUDA tensor with one weight per atom")
+    if out is None:
+        out = _held_by(torch.empty((T, 1, 3), dtype=torch.float32, device=x.device), stream)
+    rc = load().tcorr_collective(x.data_ptr(), w.data_ptr() if w is not None else None, T, N, ref_frame,
+                                 out.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_collective")
     return out
 
 

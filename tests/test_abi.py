@@ -109,6 +109,17 @@ def test_gk_and_einstein_validation(lib):
     assert gb(FAKE_X + 4, 10, 2, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 2
     assert gb(FAKE_X, 10, 3, 10, 1.0, 1.0, FAKE_X + 8 * 25, 10, None) == 1   # spans overlap
     assert gb(FAKE_X, 10, 1 << 60, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 1    # span overflows
+    col = lib.tcorr_collective
+    assert col(None, None, 10, 4, -1, FAKE_OUT, None) == 1
+    assert col(FAKE_X, None, 10, 4, -1, None, None) == 1
+    assert col(FAKE_X, None, 0, 4, -1, FAKE_OUT, None) == 1                # T < 1
+    assert col(FAKE_X, None, 10, 0, -1, FAKE_OUT, None) == 1               # N < 1
+    assert col(FAKE_X, None, 10, 4, -2, FAKE_OUT, None) == 1               # ref < -1
+    assert col(FAKE_X, None, 10, 4, 10, FAKE_OUT, None) == 1               # ref >= T
+    assert col(FAKE_X + 2, None, 10, 4, -1, FAKE_OUT, None) == 2
+    assert col(FAKE_X, FAKE_OUT + 2, 10, 4, -1, FAKE_OUT + 0x1000, None) == 2
+    assert col(FAKE_X, None, 10, 4, -1, FAKE_X + 64, None) == 1            # output inside x
+    assert col(FAKE_X, FAKE_OUT, 10, 4, -1, FAKE_OUT + 8, None) == 1       # output over the weights
     D = FAKE_OUT
     assert lib.einstein_slope(FAKE_X, 10, 1.0, 3, 5, 5, D, None) == 1     # hi <= lo
     assert lib.einstein_slope(FAKE_X, 10, 1.0, 3, 2, 10, D, None) == 1    # hi >= n
