@@ -55,6 +55,8 @@ def load_library(path: str) -> ctypes.CDLL:
     vp = ctypes.c_void_p
     lib.oracle_corr.argtypes = [ctypes.c_int, vp, i64, i64, i64, vp, i64, vp, ctypes.c_int]
     lib.oracle_corr.restype = ctypes.c_int
+    lib.oracle_corr_weighted.argtypes = [ctypes.c_int, vp, vp, i64, i64, i64, vp, i64, vp, ctypes.c_int]
+    lib.oracle_corr_weighted.restype = ctypes.c_int
     lib.oracle_xcorr.argtypes = [vp, vp, i64, i64, i64, vp, i64, vp, ctypes.c_int]
     lib.oracle_xcorr.restype = ctypes.c_int
     lib.oracle_collective.argtypes = [vp, vp, i64, i64, i64, vp]
@@ -109,6 +111,36 @@ def msd(x, tau_max=None, stride=1, lags=None, nthreads=None, lib=None):
 def acf(x, tau_max=None, stride=1, lags=None, nthreads=None, lib=None):
     """Autocorrelation <A(t0).A(t0+tau)>, the integrand of Eq. 4."""
     return corr(KIND_ACF, x, tau_max, stride, lags, nthreads, lib)
+
+
+def corr_weighted(kind: int, x: np.ndarray, w: np.ndarray, tau_max: int | None = None, stride: int = 1,
+                  lags=None, nthreads=None, lib=None) -> np.ndarray:
+    """Weighted atom average: sum_i w_i (atom i's per-lag sum) / (sum_i w_i n_o(tau))."""
+    lib = lib or _get_lib()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    T, N = x.shape[0], x.shape[1]
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    if w.shape != (N,):
+        raise ValueError("w must hold one weight per atom")
+    if lags is None:
+        if tau_max is None:
+            tau_max = T - 1
+        lags = np.arange(tau_max + 1, dtype=np.int64)
+    lags = np.ascontiguousarray(lags, dtype=np.int64)
+    out = np.zeros(lags.shape[0], dtype=np.float64)
+    rc = lib.oracle_corr_weighted(kind, x.ctypes.data, w.ctypes.data, T, N, stride, lags.ctypes.data,
+                                  lags.shape[0], out.ctypes.data, nthreads or default_threads())
+    if rc != 0:
+        raise ValueError(f"oracle_corr_weighted failed with code {rc}")
+    return out
+
+
+def msd_weighted(x, w, tau_max=None, stride=1, lags=None, nthreads=None, lib=None):
+    return corr_weighted(KIND_MSD, x, w, tau_max, stride, lags, nthreads, lib)
+
+
+def acf_weighted(x, w, tau_max=None, stride=1, lags=None, nthreads=None, lib=None):
+    return corr_weighted(KIND_ACF, x, w, tau_max, stride, lags, nthreads, lib)
 
 
 def xcf(a, b, tau_max=None, stride=1, lags=None, nthreads=None, lib=None) -> np.ndarray:

@@ -73,6 +73,7 @@ static int64_t n_origins(int64_t T, int64_t tau, int64_t s) {
 typedef struct {
     const float *x;
     const float *y;           /* kind XCF: B, the signal at the later time t0 + tau */
+    const float *w;           /* per-atom weights of the average, or NULL (equal weights) */
     int64_t T, N, s;
     const int64_t *lags;
     int64_t nlags;
@@ -118,6 +119,7 @@ static void do_block(job_t *J, int64_t b, double *traj) {
                 }
                 acc += term;
             }
+            if (J->w) acc *= (double)J->w[i];
             out[l] += acc;
         }
     }
@@ -144,7 +146,7 @@ static void *worker(void *arg) {
  * out[l] = normalised result at lags[l].  Returns 0 on success, -1 on bad
  * arguments, -2 on allocation failure.
  */
-static int corr_run(int kind, const float *x, const float *y, int64_t T, int64_t N, int64_t s,
+static int corr_run(int kind, const float *x, const float *y, const float *w, int64_t T, int64_t N, int64_t s,
                     const int64_t *lags, int64_t nlags, double *out, int nthreads) {
     if (!x || !lags || !out || T < 1 || N < 1 || s < 1 || nlags < 0) return -1;
     if (kind != ORACLE_KIND_MSD && kind != ORACLE_KIND_ACF && kind != ORACLE_KIND_XCF) return -1;
@@ -153,7 +155,7 @@ static int corr_run(int kind, const float *x, const float *y, int64_t T, int64_t
         if (lags[l] < 0 || lags[l] > T - 1) return -1;
     if (nthreads < 1) nthreads = 1;
     job_t J;
-    J.x = x; J.y = y; J.T = T; J.N = N; J.s = s; J.lags = lags; J.nlags = nlags;
+    J.x = x; J.y = y; J.w = w; J.T = T; J.N = N; J.s = s; J.lags = lags; J.nlags = nlags;
     J.kind = kind;
     J.nblocks = (N + ORACLE_BLOCK - 1) / ORACLE_BLOCK;
     J.next_block = 0;
@@ -177,10 +179,14 @@ static int corr_run(int kind, const float *x, const float *y, int64_t T, int64_t
     }
     free(th);
     if (rc) goto done;
+    double wsum = 0.0;
+    if (w)
+        for (int64_t i = 0; i < N; ++i) wsum += (double)w[i];
     for (int64_t l = 0; l < nlags; ++l) {
         double total = 0.0;
         for (int64_t b = 0; b < J.nblocks; ++b) total += J.block_sums[b * nlags + l];
-        out[l] = total / ((double)N * (double)n_origins(T, lags[l], s));
+        if (w) out[l] = total / (wsum * (double)n_origins(T, lags[l], s));
+        else out[l] = total / ((double)N * (double)n_origins(T, lags[l], s));
     }
 done:
     pthread_mutex_destroy(&J.lock);
@@ -191,7 +197,20 @@ done:
 int oracle_corr(int kind, const float *x, int64_t T, int64_t N, int64_t s,
                 const int64_t *lags, int64_t nlags, double *out, int nthreads) {
     if (kind == ORACLE_KIND_XCF) return -1;
-    return corr_run(kind, x, NULL, T, N, s, lags, nlags, out, nthreads);
+    return corr_run(kind, x, NULL, NULL, T, N, s, lags, nlags, out, nthreads);
+}
+
+/*
+ * oracle_corr_weighted: as oracle_corr, with the atom average weighted,
+ *   MSD_w(tau) = 1/(W n_o(tau)) sum_i w_i sum_{t0} sum_c (x[t0+tau][i][c] - x[t0][i][c])^2,
+ * W = sum_i w_i (likewise for the autocorrelation): the average "over all the
+ * atoms (or a subclass)" of Eq. 5 with each atom counted w_i times, e.g. a
+ * mass-weighted MSD or, with 0/1 weights, a selection.
+ */
+int oracle_corr_weighted(int kind, const float *x, const float *w, int64_t T, int64_t N, int64_t s,
+                         const int64_t *lags, int64_t nlags, double *out, int nthreads) {
+    if (kind == ORACLE_KIND_XCF || !w) return -1;
+    return corr_run(kind, x, NULL, w, T, N, s, lags, nlags, out, nthreads);
 }
 
 /*
@@ -200,7 +219,7 @@ int oracle_corr(int kind, const float *x, int64_t T, int64_t N, int64_t s,
  */
 int oracle_xcorr(const float *a, const float *b, int64_t T, int64_t N, int64_t s,
                  const int64_t *lags, int64_t nlags, double *out, int nthreads) {
-    return corr_run(ORACLE_KIND_XCF, a, b, T, N, s, lags, nlags, out, nthreads);
+    return corr_run(ORACLE_KIND_XCF, a, b, NULL, T, N, s, lags, nlags, out, nthreads);
 }
 
 /* Running Green-Kubo integral (Eq. 4, trapezoid): running[0..n-1]. */

@@ -406,10 +406,38 @@ def pin_collective(lib):
         _close(m, float((wv ** 2).sum()) * t ** 2, 1e-15, what=f"Einstein-Helfand MSD, ballistic (ref {ref})")
 
 
+# ----------------------------------------------------------------- weighted atom averages
+
+def pin_weighted(lib):
+    """Weighted atom averages: unit weights are the plain average bit for bit;
+    a one-hot weight is that atom alone; weights scaled by a power of two leave
+    the result unchanged bit for bit; integer weights equal the plain average
+    over a trajectory holding atom i w_i times."""
+    rng = np.random.default_rng(43)
+    T, N = 36, 9
+    x = rng.normal(size=(T, N, 3)).astype(np.float32)
+    wi = rng.integers(0, 4, size=N).astype(np.float32)
+    wi[0] = 2.0
+    for kind, f, fw in ((0, oracle.msd, oracle.msd_weighted), (1, oracle.acf, oracle.acf_weighted)):
+        for s in (1, 2):
+            plain = f(x, T - 1, s, lib=lib)
+            if not np.array_equal(fw(x, np.ones(N, np.float32), T - 1, s, lib=lib), plain):
+                raise AssertionError(f"weighted kind {kind} s={s}: unit weights differ from the plain average")
+            e = np.zeros(N, np.float32)
+            e[4] = 1.0
+            if not np.array_equal(fw(x, e, T - 1, s, lib=lib), f(x[:, 4:5, :], T - 1, s, lib=lib)):
+                raise AssertionError(f"weighted kind {kind} s={s}: one-hot weight is not the single atom")
+            a = fw(x, wi, T - 1, s, lib=lib)
+            if not np.array_equal(fw(x, wi * 8.0, T - 1, s, lib=lib), a):
+                raise AssertionError(f"weighted kind {kind} s={s}: not invariant under weight scaling")
+            rep = np.repeat(x, wi.astype(np.int64), axis=1)
+            _close(a, f(rep, T - 1, s, lib=lib), 1e-12, 1e-15, what=f"weighted kind {kind} s={s} vs repetition")
+
+
 ALL_PINS = [
     pin_hand_worked, pin_brute_force, pin_lag_subset, pin_fft, pin_constant_velocity,
     pin_zero_lag, pin_single_origin, pin_invariants, pin_stride_split,
     pin_gk_closed_forms, pin_einstein_exact, pin_random_walk, pin_ou,
     pin_einstein_vs_green_kubo, pin_xcf_brute_force, pin_xcf_fft, pin_xcf_closed_forms,
-    pin_collective,
+    pin_collective, pin_weighted,
 ]

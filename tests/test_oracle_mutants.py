@@ -37,6 +37,8 @@ MUTANTS = [
     ("collective_ref_ignored", "if (ref >= 0) v -= (double)x[(ref * N + i) * 3 + c];", "", 0),
     ("collective_weight_ignored", "sum += (w ? (double)w[i] : 1.0) * v;", "sum += v;", 0),
     ("collective_ref_wrong_atom", "v -= (double)x[(ref * N + i) * 3 + c];", "v -= (double)x[(ref * N) * 3 + c];", 0),
+    ("weight_ignored", "if (J->w) acc *= (double)J->w[i];", "", 0),
+    ("weighted_norm_by_atoms", "if (w) out[l] = total / (wsum *", "if (w) out[l] = total / ((double)N *", 0),
     ("collective_component_fixed", "double v = (double)x[(t * N + i) * 3 + c];",
      "double v = (double)x[(t * N + i) * 3];", 0),
 ]
