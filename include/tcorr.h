@@ -182,6 +182,29 @@ int gk_integrate_batch(const double *d_c, int64_t n, int64_t count, int64_t ldc,
                        double prefactor, double *d_running, int64_t ldr, void *stream);
 
 /*
+ * Weighted atom averages: tcorr_msd / tcorr_acf with atom i counted w_i
+ * times in Eq. 5's average "over all the atoms (or a subclass)":
+ *   MSD_w(tau) = sum_i w_i sum_{t0 in O(tau)} |x_i(t0+tau) - x_i(t0)|^2 / (W n_o(tau)),
+ *   W = sum_i w_i (likewise the autocorrelation) -- a mass-weighted MSD, or a
+ *   selection with 0/1 weights.
+ * d_w: N float32 weights on the device, 4-byte aligned, each >= 0 (a negative
+ * weight makes the result NaN), W > 0.  Method: the call writes
+ * y_i = sqrt(w_i) x_i into its workspace (for the MSD relative to the middle
+ * frame, which the MSD does not see), runs the unweighted engine of `method`
+ * on y and scales by N / W; each y value is one FP32 rounding of the exact
+ * product, so the accuracy is that of the method, plus rounding errors of the
+ * products that average out over atoms and origins.  d_ws:
+ * tcorr_weighted_workspace_size(...) bytes, 256-byte aligned (the copy of
+ * the trajectory, W, then the method's own workspace).  Other arguments and
+ * errors as tcorr_msd, plus TCORR_EINVAL for d_w == NULL.
+ */
+size_t tcorr_weighted_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method);
+int tcorr_msd_weighted(const float *d_x, const float *d_w, int64_t T, int64_t N, int64_t tau_max,
+                       int64_t stride, int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
+int tcorr_acf_weighted(const float *d_x, const float *d_w, int64_t T, int64_t N, int64_t tau_max,
+                       int64_t stride, int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Collective signal of a trajectory, the input of collective transport
  * quantities (Eq. 4 with a collective flux, as the viscosity example
  * correlates the pressure tensor of the whole box):

@@ -351,6 +351,44 @@ int tcorr_acf(const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s
     return run_corr(1, d_x, T, N, tau_max, stride, method, d_out, d_ws, ws_bytes, stream);
 }
 
+size_t tcorr_weighted_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method) {
+    const size_t eng = tcorr_workspace_size(T, N, tau_max, stride, method);
+    if (eng == 0) return 0;
+    return weighted_copy_bytes(T, N) + eng;
+}
+
+static int run_weighted(int kind, const float *d_x, const float *d_w, int64_t T, int64_t N, int64_t tau_max,
+                        int64_t s, int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!d_x || !d_w || !d_out) return TCORR_EINVAL;
+    if (!valid_sizes(T, N, tau_max, s) || !known_method(method)) return TCORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_x) & 3u) || (reinterpret_cast<uintptr_t>(d_w) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_out) & 7u) || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+        return TCORR_EALIGN;
+    const size_t need = tcorr_weighted_workspace_size(T, N, tau_max, s, method);
+    if (need == 0) return TCORR_EUNSUPPORTED;
+    if (!d_ws || ws_bytes < need) return TCORR_EWORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t copy = weighted_copy_bytes(T, N);
+    cudaError_t e = launch_weight_copy(kind, d_x, d_w, T, N, d_ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "weighted copy launch");
+    const int rc = run_corr(kind, static_cast<const float *>(d_ws), T, N, tau_max, s, method, d_out,
+                            static_cast<uint8_t *>(d_ws) + copy, ws_bytes - copy, stream);
+    if (rc != TCORR_OK) return rc;
+    e = launch_weight_rescale(d_out, tau_max + 1, T, N, d_ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "weighted rescale launch");
+    return TCORR_OK;
+}
+
+int tcorr_msd_weighted(const float *d_x, const float *d_w, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                       int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    return run_weighted(0, d_x, d_w, T, N, tau_max, stride, method, d_out, d_ws, ws_bytes, stream);
+}
+
+int tcorr_acf_weighted(const float *d_x, const float *d_w, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
+                       int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    return run_weighted(1, d_x, d_w, T, N, tau_max, stride, method, d_out, d_ws, ws_bytes, stream);
+}
+
 size_t tcorr_xcf_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method) {
     if (!valid_sizes(T, N, tau_max, stride) || !known_method(method)) return 0;
     const int m = resolve_method(method, T, N, tau_max, stride);

@@ -129,6 +129,14 @@ void prof_end(cudaStream_t st);
 // Workspace layout helpers (byte offsets, 256-byte aligned).
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// Weighted averages (weighted.cu): the scaled copy y = sqrt(w) (x - x_ref) and
+// W = sum w at the start of the workspace, then the result scaled by N / W.
+size_t weighted_copy_bytes(int64_t T, int64_t N);
+cudaError_t launch_weight_copy(int kind, const float *x, const float *w, int64_t T, int64_t N, void *d_copy,
+                               cudaStream_t st);
+cudaError_t launch_weight_rescale(double *out, int64_t n, int64_t T, int64_t N, const void *d_copy,
+                                  cudaStream_t st);
+
 // ------------------------------------------------------------------ kernels
 // Plain FP32 path: per-item per-offset partial sums (double) into `partial`
 // ([n_items][WP]).  kind 0 = MSD (differences), 1 = ACF (products), 2 =

@@ -59,6 +59,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gk_integrate_batch.restype = ci
     lib.tcorr_collective.argtypes = [vp, vp, i64, i64, i64, vp, vp]
     lib.tcorr_collective.restype = ci
+    lib.tcorr_weighted_workspace_size.argtypes = [i64, i64, i64, i64, ci]
+    lib.tcorr_weighted_workspace_size.restype = sz
+    for name in ("tcorr_msd_weighted", "tcorr_acf_weighted"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, vp, i64, i64, i64, i64, ci, vp, vp, sz, vp]
+        f.restype = ci
     lib.einstein_slope.argtypes = [vp, i64, dbl, ci, i64, i64, vp, vp]
     lib.einstein_slope.restype = ci
     lib.tcorr_batch_workspace_size.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci]
@@ -222,6 +228,42 @@ def gk_integrate_batch(c, dt: float, prefactor: float = 1.0, out=None, stream=No
     if rc != 0:
         raise TcorrError(rc, "gk_integrate_batch")
     return out
+
+
+def tcorr_weighted_workspace_size(T: int, N: int, tau_max: int, stride: int = 1, method=AUTO) -> int:
+    return int(load().tcorr_weighted_workspace_size(T, N, tau_max, stride, _method(method)))
+
+
+def _corr_weighted(fname: str, x, w, tau_max: int, stride: int, method, out, ws, stream):
+    torch = _torch()
+    _check_traj(x)
+    T, N, _ = x.shape
+    if not isinstance(w, torch.Tensor) or not w.is_cuda or w.dtype != torch.float32 or w.numel() != N \
+            or not w.is_contiguous():
+        raise TypeError("w must be a contiguous float32 CUDA tensor with one weight per atom")
+    m = _method(method)
+    if out is None:
+        out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=x.device), stream)
+    need = tcorr_weighted_workspace_size(T, N, tau_max, stride, m)
+    if ws is None:
+        ws = _held_by(_alloc_ws(need, x.device), stream)
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    rc = getattr(load(), fname)(x.data_ptr(), w.data_ptr(), T, N, tau_max, stride, m, out.data_ptr(),
+                                ws_ptr, ws_bytes, _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, fname)
+    return out
+
+
+def tcorr_msd_weighted(x, w, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, stream=None):
+    """MSD with atom i counted w[i] times (w >= 0): sum_i w_i (...) / (sum_i w_i n_o(tau))."""
+    return _corr_weighted("tcorr_msd_weighted", x, w, tau_max, stride, method, out, ws, stream)
+
+
+def tcorr_acf_weighted(x, w, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=None, stream=None):
+    """Autocorrelation with atom i counted w[i] times (w >= 0)."""
+    return _corr_weighted("tcorr_acf_weighted", x, w, tau_max, stride, method, out, ws, stream)
 
 
 def tcorr_collective(x, w=None, ref_frame: int = -1, out=None, stream=None):

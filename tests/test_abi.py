@@ -109,6 +109,15 @@ def test_gk_and_einstein_validation(lib):
     assert gb(FAKE_X + 4, 10, 2, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 2
     assert gb(FAKE_X, 10, 3, 10, 1.0, 1.0, FAKE_X + 8 * 25, 10, None) == 1   # spans overlap
     assert gb(FAKE_X, 10, 1 << 60, 10, 1.0, 1.0, FAKE_OUT, 10, None) == 1    # span overflows
+    for f in (lib.tcorr_msd_weighted, lib.tcorr_acf_weighted):
+        assert f(FAKE_X, None, 100, 10, 50, 1, 0, FAKE_OUT, FAKE_WS, 0, None) == 1          # no weights
+        assert f(None, FAKE_X, 100, 10, 50, 1, 0, FAKE_OUT, FAKE_WS, 0, None) == 1
+        assert f(FAKE_X, FAKE_X, 100, 10, 100, 1, 0, FAKE_OUT, FAKE_WS, 0, None) == 1       # tau_max >= T
+        assert f(FAKE_X, FAKE_X + 2, 100, 10, 50, 1, 0, FAKE_OUT, FAKE_WS, 0, None) == 2    # weights misaligned
+        assert f(FAKE_X, FAKE_X, 100, 10, 50, 1, 0, FAKE_OUT, FAKE_WS, 0, None) == 4        # workspace too small
+    need = lib.tcorr_weighted_workspace_size(100, 10, 50, 1, 0)
+    assert need >= 100 * 10 * 3 * 4 + lib.tcorr_workspace_size(100, 10, 50, 1, 0)
+    assert lib.tcorr_weighted_workspace_size(100, 10, 100, 1, 0) == 0
     col = lib.tcorr_collective
     assert col(None, None, 10, 4, -1, FAKE_OUT, None) == 1
     assert col(FAKE_X, None, 10, 4, -1, None, None) == 1
