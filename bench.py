@@ -54,6 +54,11 @@ WORKLOADS = {
     "viscosity": dict(label="viscosity ACF with a long window: (Pxy, Pxz, Pyz) as [T][1][3], AR(1) phi=0.999, "
                            "T=2,000,000, tau_max=500,000, ACF + running integral; FFT route vs polyphase "
                            "tensor core", T=2000000, tau_max=500000, phi=0.999),
+    "collective": dict(N=32768, T=10000, tau_max=2000, stride=1, sigma=0.005, box=5.0, gamma=0.05, sites=3,
+                       dt=1.0, label="collective quantities on the water-scale arrays (N=32768 3-site molecules, "
+                                     "SPC/E-like charges -0.8476 / +0.4238, T=10000, tau_max=2000): "
+                                     "Einstein-Helfand MSD of sum_i q_i r_i (FFT route) + charge-current ACF "
+                                     "(polyphase tensor core) + its running integral"),
     "small": dict(N=512, T=1000, tau_max=500, stride=1, sigma=0.01, box=3.0, gamma=0.1, sites=1,
                   dt=1.0, label="small MSD + VACF: N=512, T=1000, tau_max=500, stride 1"),
 }
@@ -154,6 +159,9 @@ def gpu_identifier(torch, dev):
 # from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
 # see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
 GRAM_WATER_TRAFFIC_BYTES = 8 * (982.221568e6 + 5.485568e6)
+# DRAM bytes of one collective_kernel launch on the water-scale velocities (no reference frame):
+# ncu's dram__bytes.sum.per_second x gpu__time_duration.sum; see profiles/collective_kernel_water.md.
+COLLECTIVE_WATER_TRAFFIC_BYTES = 6.622334e12 * 594.496e-6
 
 
 def peaks():
@@ -809,6 +817,123 @@ def run_viscosity_workload(args, wl):
         print(json.dumps(line), flush=True)
 
 
+def run_collective_workload(args, wl):
+    """Collective quantities on the water-scale arrays: the charge-weighted atom sums of the
+    positions (referenced to the middle frame) and of the velocities, the Einstein-Helfand
+    MSD of the first and the autocorrelation and running integral of the second.  The
+    collective kernel (one read of a 3.93 GB array) is also timed alone for its roofline, and
+    a mass-weighted MSD of the positions is timed beside the unweighted one."""
+    import torch
+    import oracle
+    from paper_1708_08619_gb300 import build as tbuild
+    from paper_1708_08619_gb300 import synth, tcorr
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tbuild.build()
+    tcorr.load()
+    N, T, tm = wl["N"], wl["T"], wl["tau_max"]
+    seed = synth.BASE_SEED + 100 * rank
+    x = synth.random_walk_positions_device(T, N, wl["sigma"], wl["box"], seed, device=dev,
+                                           sites_per_molecule=wl["sites"])
+    v = synth.ou_velocities_device(T, N, wl["gamma"], 1.0, seed + 1, device=dev)
+    site = torch.arange(N, device=dev) % 3
+    q = torch.where(site == 0, -0.8476, 0.4238).to(torch.float32)
+    mass = torch.where(site == 0, 15.999, 1.008).to(torch.float32)
+    jx = torch.empty((T, 1, 3), dtype=torch.float32, device=dev)
+    jv = torch.empty_like(jx)
+    m_eh = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+    c_j = torch.empty_like(m_eh)
+    gk = torch.empty_like(m_eh)
+    ws_eh = torch.empty(max(256, tcorr.tcorr_workspace_size(T, 1, tm, 1, "fft")), dtype=torch.uint8, device=dev)
+    ws_c = torch.empty(max(256, tcorr.tcorr_workspace_size(T, 1, tm, 1, args.method)), dtype=torch.uint8,
+                       device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def step():
+        tcorr.tcorr_collective(x, q, T // 2, out=jx, stream=stream)
+        tcorr.tcorr_msd(jx, tm, 1, "fft", out=m_eh, ws=ws_eh, stream=stream)
+        tcorr.tcorr_collective(v, q, -1, out=jv, stream=stream)
+        tcorr.tcorr_acf(jv, tm, 1, args.method, out=c_j, ws=ws_c, stream=stream)
+        tcorr.gk_integrate(c_j, wl["dt"], 1.0, out=gk, stream=stream)
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        stream.synchronize()
+        sampler = ClockSampler(gpu_identifier(torch, local))
+        sampler.start()
+        time.sleep(0.3)
+        ms = timed(step, args.steps)
+        clocks = sampler.stop()
+        col_ms = timed(lambda: tcorr.tcorr_collective(x, q, -1, out=jx, stream=stream), 10)
+        col_ref_ms = timed(lambda: tcorr.tcorr_collective(x, q, T // 2, out=jx, stream=stream), 10)
+        ws_w = torch.empty(tcorr.tcorr_weighted_workspace_size(T, N, tm, 1, args.method), dtype=torch.uint8,
+                           device=dev)
+        mo = torch.empty(tm + 1, dtype=torch.float64, device=dev)
+        tcorr.tcorr_msd_weighted(x, mass, tm, 1, args.method, out=mo, ws=ws_w, stream=stream)
+        w_ms = timed(lambda: tcorr.tcorr_msd_weighted(x, mass, tm, 1, args.method, out=mo, ws=ws_w,
+                                                       stream=stream), 3)
+        u_ms = timed(lambda: tcorr.tcorr_msd(x, tm, 1, args.method, out=mo, ws=ws_w, stream=stream), 3)
+        del ws_w
+    err = None
+    if not args.no_cpu_baseline and rank == 0:
+        # the oracle chain on a frame subset is too slow at this size; check the collective
+        # signal itself on 16 frames and the correlations of the device-formed signals
+        fr = np.linspace(0, T - 1, 16).astype(np.int64)
+        xs = x[fr].cpu().numpy()
+        xr = x[T // 2].cpu().numpy()[None]
+        qh = q.cpu().numpy()
+        want = oracle.collective(np.concatenate([xs, xr]), qh, len(fr))[:-1]
+        got = jx[fr].cpu().numpy().reshape(-1, 3)
+        lags = np.array([0, 1, 2, 10, 100, 1000, tm])
+        jxh, jvh = jx.cpu().numpy(), jv.cpu().numpy()
+        tcorr.tcorr_collective(x, q, T // 2, out=jx, stream=stream)
+        tcorr.tcorr_msd(jx, tm, 1, "fft", out=m_eh, ws=ws_eh, stream=stream)
+        tcorr.tcorr_acf(jv, tm, 1, args.method, out=c_j, ws=ws_c, stream=stream)
+        stream.synchronize()
+        rm = oracle.msd(jxh, stride=1, lags=lags)
+        rc = oracle.acf(jvh, stride=1, lags=lags)
+        err = {"collective_max_abs_over_max": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
+               "eh_msd_over_msd_tau_max": float(np.max(np.abs(m_eh.cpu().numpy()[lags] - rm)) / rm[-1]),
+               "current_acf_over_c0": float(np.max(np.abs(c_j.cpu().numpy()[lags] - rc)) / abs(rc[0])),
+               "lags": lags.tolist()}
+    pk, pk_kind = peaks()
+    gbs = 12.0 * N * T / (col_ms / 1000.0) / 1e9
+    line = {"metric": "atom.frame terms/s of the collective sums", "value": 2.0 * N * T * world / (ms / 1000.0),
+            "unit": "atom-frames/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 compensated sums; f64 transforms (EH MSD); " + args.method + " (current ACF)",
+            "data": "synthetic",
+            "config": {"workload": wl["label"], "N": N, "T": T, "tau_max": tm,
+                       "collective_ms": col_ms, "collective_ref_ms": col_ref_ms,
+                       "mass_weighted_msd_ms": w_ms, "unweighted_msd_ms": u_ms,
+                       "error_vs_oracle": err, "l2": "inputs larger than L2 (2 x 3.93 GB), no flush"},
+            "clocks": clocks, "e2e": None,
+            # per step: 2 collective, FFT-route MSD (gather, power, lag sum, S, S prefix, finalize;
+            # the transforms are cuFFT's), polyphase ACF (row max, split, Gram, reduce), Green-Kubo
+            "gpu_launches": 13 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                         "frac": gbs / pk.get("hbm_gbs", 6800.0),
+                         "traffic": COLLECTIVE_WATER_TRAFFIC_BYTES if (N, T) == (32768, 10000) else None,
+                         "kernel": "collective_kernel",
+                         "note": f"12 bytes per atom and frame read once / the kernel alone (CUDA events "
+                                 f"around 10 launches, no reference frame), {pk_kind} copy bandwidth"},
+            "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,6 +956,8 @@ def main():
         run_flux_workload(args, wl)
     elif args.workload == "viscosity":
         run_viscosity_workload(args, wl)
+    elif args.workload == "collective":
+        run_collective_workload(args, wl)
     else:
         run_gpu(args, wl)
 
