@@ -333,14 +333,19 @@ def run_gpu(args, wl):
     e2e_steps = max(1, min(args.steps, 5))
 
     def timed_e2e(fn):
+        # each step ends with its results read back to the host (a stream synchronise), so
+        # steps are timed one by one; the median keeps one slow step of the shared host link
+        # from setting the number
         fn()
         torch.cuda.synchronize()
         barrier()
-        t0 = time.perf_counter()
+        per = []
         for _ in range(e2e_steps):
+            t0 = time.perf_counter()
             fn()
-        torch.cuda.synchronize()
-        return shard.max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+            torch.cuda.synchronize()
+            per.append(time.perf_counter() - t0)
+        return shard.max_over_ranks(statistics.median(per))
 
     def finish_on(st):
         # GK + Einstein, then the results back to pinned host memory
