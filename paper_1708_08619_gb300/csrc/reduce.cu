@@ -30,14 +30,28 @@ __device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t 
     const int64_t ncs = c_hi - c_lo + 1;
     const int64_t nterm = a.n_groups * a.n_rows * ncs;
     double sum = 0.0;
+    // term t = (gg, rr, cc) with cc fastest; the lane's first term is decoded
+    // once and each step of 32 terms is added as mixed-radix carries (no
+    // 64-bit division in the loop; the same terms in the same order)
+    int64_t cc = lane % ncs, q = lane / ncs;
+    int64_t rr = q % a.n_rows, gg = q / a.n_rows;
+    const int64_t dc = 32 % ncs, dq = 32 / ncs;
     for (int64_t t = lane; t < nterm; t += 32) {
-        const int64_t cc = t % ncs;
-        const int64_t rr = (t / ncs) % a.n_rows;
-        const int64_t gg = t / (ncs * a.n_rows);
         const int64_t c = c_lo + cc;
         const int64_t item = ((gg * a.n_res + rho) * a.n_rows + rr) * a.n_cols + c;
         const int64_t w = m - c * a.BF + a.BO - 1;
         sum += a.partial[item * a.WP + w];
+        cc += dc;
+        int64_t carry = dq;
+        if (cc >= ncs) {
+            cc -= ncs;
+            ++carry;
+        }
+        rr += carry;
+        while (rr >= a.n_rows) {
+            rr -= a.n_rows;
+            ++gg;
+        }
     }
     const double D = warp_sum(sum);
     if (lane == 0) {
