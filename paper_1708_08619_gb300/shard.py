@@ -51,14 +51,16 @@ def atom_range(N: int, rank: int, world: int):
     return a0, a0 + base + (1 if rank < extra else 0)
 
 
-def combine_atom_shards(result, n_local: int, group=None):
+def combine_atom_shards(result, n_local: float, group=None):
     """Whole-trajectory average from per-rank results over disjoint atom slices.
 
     Every per-lag MSD / autocorrelation value is an average over atoms and
     origins; the origin count n_o(tau) is the same on every rank (same T and
     stride), so the average over all atoms is sum_r N_r result_r / sum_r N_r:
-    one FP64 all-reduce of tau_max + 2 values.  Works on any backend (NCCL with
-    CUDA tensors, gloo with CPU tensors); identity without a process group."""
+    one FP64 all-reduce of tau_max + 2 values.  For weighted averages n_local
+    is the rank's weight sum W_r instead of its atom count.  Works on any
+    backend (NCCL with CUDA tensors, gloo with CPU tensors); identity without a
+    process group."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()):

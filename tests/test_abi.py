@@ -157,6 +157,23 @@ def test_binding_refuses_cpu_tensors(lib):
         tcorr.tcorr_msd(x, 5)
 
 
+def test_bindings_of_the_added_calls_refuse_bad_tensors(lib):
+    """The bindings check their tensors before calling the library (no device needed)."""
+    torch = pytest.importorskip("torch")
+    x = torch.zeros((10, 2, 3), dtype=torch.float32)
+    w = torch.ones(2, dtype=torch.float32)
+    c = torch.zeros((3, 10), dtype=torch.float64)
+    for call in (lambda: tcorr.tcorr_collective(x),                         # CPU trajectory
+                 lambda: tcorr.tcorr_msd_weighted(x, w, 5),
+                 lambda: tcorr.tcorr_acf_weighted(x, w, 5),
+                 lambda: tcorr.tcorr_xcf(x, x, 5),
+                 lambda: tcorr.gk_integrate_batch(c, 1.0),                  # CPU series
+                 lambda: tcorr.gk_integrate_batch(c[0], 1.0),               # not 2-D
+                 lambda: tcorr.tcorr_msd_stream(x.double(), 5)):            # not float32
+        with pytest.raises(TypeError):
+            call()
+
+
 def call_msd_stream(lib, x=FAKE_X, T=100, N=10, tau_max=50, s=1, method=0, chunk=0, out=FAKE_OUT,
                     ws=FAKE_WS, ws_bytes=0):
     return lib.tcorr_msd_stream(x, T, N, tau_max, s, method, chunk, out, ws, ws_bytes, None)

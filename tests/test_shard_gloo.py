@@ -114,3 +114,41 @@ def test_two_gloo_ranks_combine_atom_shards():
     want = oracle.msd(synth.random_walk_positions(120, 37, 0.02, 2.0, seed=91), 60, 2)
     for _, got in results:
         np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+
+
+def _weighted_atom_worker(rank, world, port, q):
+    import torch.distributed as dist
+    import oracle
+    from paper_1708_08619_gb300 import synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    v = synth.ou_velocities(150, 41, 0.1, 1.0, seed=93)
+    w = np.random.default_rng(94).uniform(0.5, 16.0, size=41).astype(np.float32)
+    a0, a1 = shard.atom_range(41, rank, world)
+    # a weighted share is combined with its weight sum in place of its atom count
+    part = torch.from_numpy(oracle.acf_weighted(np.ascontiguousarray(v[:, a0:a1]), w[a0:a1], 70, 1))
+    whole = shard.combine_atom_shards(part, float(w[a0:a1].astype(np.float64).sum()))
+    dist.destroy_process_group()
+    q.put((rank, whole.numpy()))
+
+
+def test_two_gloo_ranks_combine_weighted_atom_shards():
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_1708_08619_gb300 import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_weighted_atom_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    v = synth.ou_velocities(150, 41, 0.1, 1.0, seed=93)
+    w = np.random.default_rng(94).uniform(0.5, 16.0, size=41).astype(np.float32)
+    want = oracle.acf_weighted(v, w, 70, 1)
+    for _, got in results:
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
