@@ -105,7 +105,9 @@ typedef enum {
 /*
  * Bytes of device workspace that tcorr_msd / tcorr_acf need for these
  * arguments and this method.  Returns 0 when the arguments are invalid (the
- * call itself then reports the error).  Pure host function; no CUDA call.
+ * call itself then reports the error).  Host arithmetic only, except for the
+ * FFT route (TCORR_FFT, or TCORR_AUTO when it picks that route), whose size
+ * comes from a cuFFT plan made on the current device.
  */
 size_t tcorr_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride,
                             int method);
