@@ -201,6 +201,12 @@ def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    if args.workload not in ("water", "water8", "mid", "small"):
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the reference arm times the oracle on the MSD + VACF workloads "
+                                         "(water, water8, mid, small); this workload has no such line"}),
+              flush=True)
+        return
     from paper_1708_08619_gb300 import synth
     xh = synth.random_walk_positions(wl["T"], wl["N"], wl["sigma"], wl["box"], synth.BASE_SEED,
                                      sites_per_molecule=wl["sites"])
@@ -215,7 +221,7 @@ def run_reference(args, wl):
         tot_t += el
     value = float(statistics.median(rates))
     sample = (f"per step: MSD and VACF at {nl} evenly spaced lags in [0, {wl['tau_max']}], all "
-              f"atoms and origins, on the full water-scale arrays (numpy-drawn, same recipe)")
+              f"atoms and origins, on the workload's full arrays (numpy-drawn, same recipe)")
     line = {"impl": "reference", "metric": "atom.origin.lag updates/s (MSD+ACF)", "value": value,
             "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * tot_t / max(1, args.steps), "higher_is_better": True,

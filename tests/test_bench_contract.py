@@ -36,9 +36,14 @@ def test_reference_arm_prints_one_contract_line():
         assert abs(ups / (d["ms_per_step"] / 1e3) / d["value"] - 1) < 0.05
 
 
+def test_reference_arm_on_a_workload_without_an_oracle_line():
+    d = run_bench("--impl", "reference", "--workload", "batch", "--steps", "1", "--warmup", "3")
+    assert d["impl"] == "reference" and "unavailable" in d
+
+
 def test_help_lists_the_workloads():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
                        cwd=ROOT, timeout=120)
     assert r.returncode == 0
-    for w in ("water", "batch", "flux", "viscosity"):
+    for w in ("water", "batch", "flux", "viscosity", "collective"):
         assert w in r.stdout
