@@ -2,8 +2,9 @@
 
 Each translation unit under csrc/ is compiled in parallel to an object in
 ``_build/``, then linked into ``paper_1708_08619_gb300/libtcorr.so``.  The
-library links only the CUDA runtime; the driver entry point it needs
-(tensor-map encoding) is looked up at run time.
+library links the CUDA runtime and cuFFT (the transforms of the FFT route);
+the driver entry point it needs (tensor-map encoding) is looked up at run
+time.
 """
 from __future__ import annotations
 

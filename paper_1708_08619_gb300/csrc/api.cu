@@ -301,8 +301,6 @@ int batch_run_graph(const tcorr_instance *items, int count, int m, void *d_ws, s
 
 }  // namespace
 
-// The plain path's plan and size check, shared with the fixed-scratch entry
-// point so that both produce bit-identical results for the same arguments.
 // Cross-correlation: products of d_a at the origin and d_b at the later frame,
 // band form on either path (no polyphase: its operand copies hold one signal).
 int run_xcf(const float *d_a, const float *d_b, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
@@ -319,6 +317,8 @@ int run_xcf(const float *d_a, const float *d_b, int64_t T, int64_t N, int64_t ta
     return plain_run(2, d_a, T, N, tau_max, s, d_out, d_ws, ws_bytes, st, nullptr, d_b);
 }
 
+// The plain path's plan and size check, shared with the fixed-scratch entry
+// point so that both produce bit-identical results for the same arguments.
 BandPlan plain_band_plan(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     return make_band_plan(T, N, tau_max, s, plain_tile_bo(), plain_tile_bf(), kPlainKseg, kMinItems);
 }

@@ -287,7 +287,8 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulate, A/B K-major, M = 128, N = 256.
+// Instruction descriptor: FP32 accumulate, A/B K-major, M = 128, N = BF = 192
+// (the narrow last tile of a band row overrides N per item).
 template <int PREC>
 __host__ __device__ constexpr uint32_t make_idesc() {
     return (1u << 4)                                                       // D format F32

@@ -119,6 +119,26 @@ def _check_traj(x):
         raise TypeError("x must be a contiguous float32 tensor of shape [T][N][3]")
 
 
+def _check_out(out, n: int, device, dtype_name: str = "float64"):
+    """A caller's output tensor: contiguous, of the result's dtype, on the input's
+    device, with room for n values; raises TypeError before any library call."""
+    torch = _torch()
+    dtype = getattr(torch, dtype_name)
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.device != torch.device(device):
+        raise TypeError("out must be a CUDA tensor on the input's device")
+    if out.dtype != dtype or not out.is_contiguous() or out.numel() < n:
+        raise TypeError(f"out must be a contiguous {dtype_name} tensor of at least {n} values")
+    return out
+
+
+def _check_ws(ws, device):
+    torch = _torch()
+    if ws is not None and (not isinstance(ws, torch.Tensor) or not ws.is_cuda
+                           or ws.device != torch.device(device) or not ws.is_contiguous()):
+        raise TypeError("ws must be a contiguous CUDA tensor on the input's device")
+    return ws
+
+
 def tcorr_workspace_size(T: int, N: int, tau_max: int, stride: int = 1, method=AUTO) -> int:
     return int(load().tcorr_workspace_size(T, N, tau_max, stride, _method(method)))
 
@@ -147,6 +167,8 @@ def _corr(fname: str, x, tau_max: int, stride: int, method, out, ws, stream):
     m = _method(method)
     if out is None:
         out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=x.device), stream)
+    _check_out(out, tau_max + 1, x.device)
+    _check_ws(ws, x.device)
     need = tcorr_workspace_size(T, N, tau_max, stride, m)
     if ws is None:
         ws = _held_by(_alloc_ws(need, x.device), stream)
@@ -182,8 +204,12 @@ def tcorr_xcf(a, b, tau_max: int, stride: int = 1, method=AUTO, out=None, ws=Non
         raise TypeError("a and b must have the same shape")
     T, N, _ = a.shape
     m = _method(method)
+    if a.device != b.device:
+        raise TypeError("a and b must be on the same device")
     if out is None:
         out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=a.device), stream)
+    _check_out(out, tau_max + 1, a.device)
+    _check_ws(ws, a.device)
     need = tcorr_xcf_workspace_size(T, N, tau_max, stride, m)
     if ws is None:
         ws = _held_by(_alloc_ws(need, a.device), stream)
@@ -203,6 +229,7 @@ def gk_integrate(c, dt: float, prefactor: float = 1.0, out=None, stream=None):
         raise TypeError("c must be a contiguous float64 CUDA tensor")
     if out is None:
         out = _held_by(torch.empty_like(c), stream)
+    _check_out(out, c.numel(), c.device)
     rc = load().gk_integrate(c.data_ptr(), c.numel(), dt, prefactor, out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "gk_integrate")
@@ -242,8 +269,12 @@ def _corr_weighted(fname: str, x, w, tau_max: int, stride: int, method, out, ws,
             or not w.is_contiguous():
         raise TypeError("w must be a contiguous float32 CUDA tensor with one weight per atom")
     m = _method(method)
+    if w.device != x.device:
+        raise TypeError("w must be on the trajectory's device")
     if out is None:
         out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=x.device), stream)
+    _check_out(out, tau_max + 1, x.device)
+    _check_ws(ws, x.device)
     need = tcorr_weighted_workspace_size(T, N, tau_max, stride, m)
     if ws is None:
         ws = _held_by(_alloc_ws(need, x.device), stream)
@@ -274,8 +305,11 @@ def tcorr_collective(x, w=None, ref_frame: int = -1, out=None, stream=None):
     T, N, _ = x.shape
     if w is not None and (not w.is_cuda or w.dtype != torch.float32 or w.numel() != N or not w.is_contiguous()):
         raise TypeError("w must be a contiguous float32 CUDA tensor with one weight per atom")
+    if w is not None and w.device != x.device:
+        raise TypeError("w must be on the trajectory's device")
     if out is None:
         out = _held_by(torch.empty((T, 1, 3), dtype=torch.float32, device=x.device), stream)
+    _check_out(out, 3 * T, x.device, "float32")
     rc = load().tcorr_collective(x.data_ptr(), w.data_ptr() if w is not None else None, T, N, ref_frame,
                                  out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
@@ -296,6 +330,7 @@ def einstein_slope(msd, dt: float, dim: int = 3, lo: int | None = None, hi: int 
         lo = -(-(2 * hi) // 10)
     if out is None:
         out = _held_by(torch.empty(2, dtype=torch.float64, device=msd.device), stream)
+    _check_out(out, 2, msd.device)
     rc = load().einstein_slope(msd.data_ptr(), n, dt, dim, lo, hi, out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "einstein_slope")
@@ -347,6 +382,8 @@ def _corr_stream(fname: str, x, tau_max: int, stride: int, method, chunk_frames:
     device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     if out is None:
         out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=device), stream)
+    _check_out(out, tau_max + 1, device)
+    _check_ws(ws, device)
     need = tcorr_stream_workspace_size(T, N, tau_max, stride, m, chunk_frames)
     if ws is None:
         ws = _held_by(_alloc_ws(need, device), stream)
@@ -379,6 +416,7 @@ def tcorr_plain_static(kind: int, x, tau_max: int, stride: int = 1, out=None, st
     _check_traj(x)
     if out is None:
         out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=x.device), stream)
+    _check_out(out, tau_max + 1, x.device)
     rc = load().tcorr_plain_static(kind, x.data_ptr(), x.shape[0], x.shape[1], tau_max, stride,
                                    out.data_ptr(), _stream_ptr(stream))
     if rc != 0:

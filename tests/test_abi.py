@@ -1,8 +1,18 @@
 """The C ABI: the library builds, loads, exports every declared symbol, and
-rejects bad arguments on the host before any CUDA work (CPU only)."""
+rejects bad arguments on the host before any CUDA work (CPU only).
+
+The calls below pass made-up device addresses that are never mapped; they are
+safe only because validation rejects every one of them on the host.  So that a
+regression in validation can never launch a kernel on such an address, the
+checks that use the library run in a child process in which no CUDA device is
+visible (CUDA_VISIBLE_DEVICES empty before CUDA starts): a launch that slipped
+through would fail there with a CUDA error instead of touching a GPU.
+"""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -10,10 +20,24 @@ from paper_1708_08619_gb300 import build as tbuild
 from paper_1708_08619_gb300 import tcorr
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CHILD = os.environ.get("TCORR_ABI_CHILD") == "1"
+
+
+def test_library_checks_in_a_process_without_cuda_devices():
+    if CHILD:
+        pytest.skip("this is the child process")
+    tbuild.build()
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", TCORR_ABI_CHILD="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.abspath(__file__), "-q", "-x",
+                        "-p", "no:cacheprovider"], env=env, cwd=ROOT, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
 
 
 @pytest.fixture(scope="module")
 def lib():
+    if not CHILD:
+        pytest.skip("runs in the child process with no CUDA device visible")
     path = tbuild.build()
     return tcorr.load(path)
 
