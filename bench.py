@@ -8,14 +8,17 @@ GPU through the C ABI.  Metric: atom.origin.lag updates per second, where an
 update is one (atom, origin, lag) triple; MSD and autocorrelation updates are
 counted separately and summed.
 
-Default workload: water scale, N = 32768 atoms (3-site molecules), T = 10000
-frames, tau_max = 2000, origin stride 1; positions are a random walk
-(sigma = 0.005 nm per axis per frame, 5 nm box), velocities an OU process
-(gamma = 0.05 per frame, sigma = 1).  Both arrays (3.93 GB each) are larger
-than L2, so no flush is needed between steps.
+Default workload: the precision configuration, the largest single-GPU one:
+N = 100000 atoms, T = 20000 frames, tau_max = 10000, origin stride 1;
+positions start uniform in [0, 100) nm (large offsets stress the
+cancellation of the split form) plus a random walk of sigma = 0.005 nm per
+axis per frame, velocities an OU process (gamma = 0.05 per frame, sigma = 1).
+Each array is 24 GB, far larger than L2, so no flush is needed between
+steps.  `--workload water` runs the water-scale configuration (N = 32768
+3-site molecules, T = 10000, tau_max = 2000).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--method M]
-       [--impl reference]   (times the FP64 CPU oracle instead)
+       [--workload W] [--impl reference]   (times the FP64 CPU oracle instead)
 Under torchrun each rank runs its own instance (seed + rank) with no
 exchange between ranks (weak scaling).
 """
@@ -35,6 +38,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "precision": dict(N=100000, T=20000, tau_max=10000, stride=1, sigma=0.005, box=100.0, gamma=0.05,
+                      sites=1, dt=1.0, stream_chunk=2500,
+                      label="precision MSD + VACF + GK + Einstein: N=100000, T=20000, tau_max=10000, "
+                            "stride 1, positions offset up to 100 nm"),
+    "precision16": dict(N=6250, T=20000, tau_max=10000, stride=1, sigma=0.005, box=100.0, gamma=0.05,
+                        sites=1, dt=1.0, stream_chunk=2500,
+                        label="precision shape with 1/16 of the atoms (profiling case): N=6250, T=20000, "
+                              "tau_max=10000, stride 1, positions offset up to 100 nm"),
     "water": dict(N=32768, T=10000, tau_max=2000, stride=1, sigma=0.005, box=5.0, gamma=0.05,
                   sites=3, dt=1.0,
                   label="water-scale MSD + VACF + GK + Einstein: N=32768 (3-site molecules), "
@@ -155,12 +166,13 @@ def gpu_identifier(torch, dev):
         return dev
 
 
-# DRAM bytes (read + write) of one water-scale MSD launch of the tensor-core band kernel (FP16 x3),
-# from ncu on the 1/8-atom profiling case times 8 (traffic scales with N at fixed T and tau_max);
-# see profiles/gram_band_kernel_water.md.  Valid for the kernel as captured there.
-GRAM_WATER_TRAFFIC_BYTES = 8 * (982.221568e6 + 5.485568e6)
+# DRAM bytes (read + write) per launch of the dominant kernel, from ncu captures of the kernel as
+# built now, per workload.  A capture too large for ncu is taken on the 1/8- or 1/16-atom case
+# of the same T and tau_max and scaled by the atom ratio: operand bytes, tiles and updates all
+# scale with N there.  A workload or method without an entry reports null.
+GRAM_TRAFFIC_BYTES = {("water", "fp16x3"): 8 * (982.221568e6 + 5.485568e6)}
 # DRAM bytes of one collective_kernel launch on the water-scale velocities (no reference frame):
-# ncu's dram__bytes.sum.per_second x gpu__time_duration.sum; see profiles/collective_kernel_water.md.
+# ncu's dram__bytes.sum.per_second x gpu__time_duration.sum.
 COLLECTIVE_WATER_TRAFFIC_BYTES = 6.622334e12 * 594.496e-6
 
 
@@ -176,58 +188,81 @@ def peaks():
 
 # ------------------------------------------------------------------ oracle arm
 
-def oracle_sample(xh, vh, wl, target_s):
-    """Time the FP64 oracle on a bounded sample of the workload's lags."""
+def oracle_lags(wl):
+    """The lags at which the oracle is evaluated, both for the GPU arm's error
+    check and CPU baseline and for the reference arm: 24 evenly spaced lags in
+    [0, tau_max], lags 1 and 2, and 16 lags spread over the last 192 lags (the
+    last column tile of every band row of the tensor-core kernel)."""
+    tm = wl["tau_max"]
+    spread = np.linspace(0, tm, 24).astype(np.int64)
+    tail = np.linspace(max(0, tm - 191), tm, 16).astype(np.int64)
+    return np.unique(np.concatenate([spread, [1, 2], tail]).clip(0, tm))
+
+
+def oracle_pass(xh, vh, s, lags, nthreads=None):
+    """MSD of xh and autocorrelation of vh at `lags` by the FP64 oracle; returns
+    (MSD values, ACF values, seconds, updates)."""
     import oracle
-    T, tm, s = wl["T"], wl["tau_max"], wl["stride"]
-    N = xh.shape[1]
-    cores = oracle.default_threads()
-    # calibrate on two lags, then size the sample to about target_s seconds
-    probe = np.array([1, tm], dtype=np.int64)
+    T, N = xh.shape[0], xh.shape[1]
     t0 = time.perf_counter()
-    oracle.msd(xh, stride=s, lags=probe)
-    t_probe = time.perf_counter() - t0
-    n_lags = int(max(2, min(tm + 1, target_s / max(t_probe, 1e-3))))
-    lags = np.unique(np.linspace(0, tm, n_lags).astype(np.int64))
-    t0 = time.perf_counter()
-    m_ref = oracle.msd(xh, stride=s, lags=lags)
-    c_ref = oracle.acf(vh, stride=s, lags=lags)
+    m_ref = oracle.msd(xh, stride=s, lags=lags, nthreads=nthreads)
+    c_ref = oracle.acf(vh, stride=s, lags=lags, nthreads=nthreads)
     el = time.perf_counter() - t0
     n_up = 2 * int(sum(N * ((T - 1 - int(l)) // s + 1) for l in lags))
-    return n_up / el, cores, len(lags), el, (lags, m_ref, c_ref)
+    return m_ref, c_ref, el, n_up
 
 
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    if args.workload not in ("water", "water8", "mid", "small"):
+    if args.workload not in ("precision", "precision16", "water", "water8", "mid", "small"):
         print(json.dumps({"impl": "reference",
                           "unavailable": "the reference arm times the oracle on the MSD + VACF workloads "
-                                         "(water, water8, mid, small); this workload has no such line"}),
+                                         "(precision, water, their profiling cases, mid, small); this "
+                                         "workload has no such line"}),
               flush=True)
         return
+    import oracle
     from paper_1708_08619_gb300 import synth
-    xh = synth.random_walk_positions(wl["T"], wl["N"], wl["sigma"], wl["box"], synth.BASE_SEED,
-                                     sites_per_molecule=wl["sites"])
-    vh = synth.ou_velocities(wl["T"], wl["N"], wl["gamma"], 1.0, synth.BASE_SEED + 1)
+    T, tm, s = wl["T"], wl["tau_max"], wl["stride"]
+    lags = oracle_lags(wl)
+    cores = oracle.default_threads()
+    # each step: the oracle at the GPU arm's lags over a slice of the atoms sized to about
+    # TCORR_REF_STEP_S seconds (every atom is an independent draw of the same recipe, so a
+    # slice is a sample of the same workload); calibrated on one 64-atom block per thread
     per_step = float(os.environ.get("TCORR_REF_STEP_S", "3.0"))
+    n_cal = min(wl["N"], 64 * cores)
+    xc = synth.random_walk_positions(T, n_cal, wl["sigma"], wl["box"], synth.BASE_SEED,
+                                     sites_per_molecule=wl["sites"])
+    vc = synth.ou_velocities(T, n_cal, wl["gamma"], 1.0, synth.BASE_SEED + 1)
+    el_cal = oracle_pass(xc, vc, s, lags)[2]
+    blocks = max(1, int(per_step / max(el_cal, 1e-3)))
+    n_sub = int(min(wl["N"], n_cal * blocks))
+    if n_sub > n_cal:
+        xh = synth.random_walk_positions(T, n_sub, wl["sigma"], wl["box"], synth.BASE_SEED,
+                                         sites_per_molecule=wl["sites"])
+        vh = synth.ou_velocities(T, n_sub, wl["gamma"], 1.0, synth.BASE_SEED + 1)
+    else:
+        xh, vh = xc, vc
+    del xc, vc
     for _ in range(args.warmup):
-        oracle_sample(xh, vh, wl, per_step / 4)[:4]
-    rates, tot_t, cores, nl = [], 0.0, 1, 0
+        oracle_pass(xh, vh, s, lags)
+    rates, tot_t, n_up = [], 0.0, 0
     for _ in range(args.steps):
-        r, cores, nl, el = oracle_sample(xh, vh, wl, per_step)[:4]
-        rates.append(r)
+        _, _, el, n_up = oracle_pass(xh, vh, s, lags)
+        rates.append(n_up / el)
         tot_t += el
     value = float(statistics.median(rates))
-    sample = (f"per step: MSD and VACF at {nl} evenly spaced lags in [0, {wl['tau_max']}], all "
-              f"atoms and origins, on the workload's full arrays (numpy-drawn, same recipe)")
+    sample = (f"per step: MSD and VACF at the GPU arm's {len(lags)} oracle lags in [0, {tm}], all origins, "
+              f"{n_sub} of the {wl['N']} atoms (numpy-drawn, same recipe)")
     line = {"impl": "reference", "metric": "atom.origin.lag updates/s (MSD+ACF)", "value": value,
             "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * tot_t / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["label"], "N": wl["N"], "T": wl["T"], "tau_max": wl["tau_max"],
-                       "stride": wl["stride"], "method": "oracle (FP64 CPU)"},
+            "config": {"workload": wl["label"], "N": wl["N"], "T": T, "tau_max": tm,
+                       "stride": s, "method": "oracle (FP64 CPU)", "updates_per_step": n_up,
+                       "atoms_per_step": n_sub, "lags_per_step": int(len(lags))},
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
@@ -240,7 +275,7 @@ def run_reference(args, wl):
 def run_gpu(args, wl):
     import torch
     from paper_1708_08619_gb300 import build as tbuild
-    from paper_1708_08619_gb300 import synth, tcorr
+    from paper_1708_08619_gb300 import shard, synth, tcorr
 
     world, rank, local = dist_env()
     if world > 1:
@@ -263,10 +298,11 @@ def run_gpu(args, wl):
     out_gk = torch.empty(tm + 1, dtype=torch.float64, device=dev)
     out_D = torch.empty(2, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # plain: tile + reduce (MSD), tile + reduce (ACF), GK, Einstein
-    # tensor core: split + S combine + S prefix + gram + reduce (MSD), split + gram + reduce (ACF),
-    # GK, Einstein (the ncu launch list in profiles/gram_band_kernel_water.md shows the ten)
-    launches_per_step = 6 if method == "plain" else 10
+    # this library's launches per step -- plain: tile + reduce (MSD), tile + reduce (ACF), GK,
+    # Einstein; tensor core: split + S combine + S prefix + Gram + reduce (MSD), split + Gram +
+    # reduce (ACF), GK (one launch up to 32 blocks of 2048 lags), Einstein
+    gk_launches = 1 if tm + 1 <= 32 * 2048 else 3
+    launches_per_step = (5 if method == "plain" else 9) + gk_launches
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     msd_ms, acf_ms = [], []
@@ -320,18 +356,124 @@ def run_gpu(args, wl):
     if tcorr.tcorr_status_poll() != 0:
         raise RuntimeError("device status word set during the timed region")
 
-    from paper_1708_08619_gb300 import shard
     ms_per_step = shard.max_over_ranks(elapsed_ms / args.steps)
     m_dev = out_m.cpu().numpy().copy()       # the timed steps' results (checked against the oracle below)
     c_dev = out_c.cpu().numpy().copy()
-    u_step = updates(N, T, tm, s) * 2
+    u_res = updates(N, T, tm, s)
+    u_step = 2 * u_res
     value = u_step * world / (ms_per_step / 1000.0)
 
-    # ---- end to end through the public API from pinned host memory
+    # ---- roofline of the dominant kernel (the MSD kernel), timed alone
+    pk, pk_kind = peaks()
+    msd_avg_s = kern_msd[0] / max(1, kern_msd[1]) / 1000.0
+    acf_avg_s = kern_acf[0] / max(1, kern_acf[1]) / 1000.0
+    if method == "plain":
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak_ops = 152 * 128 * sm_mhz * 1e6 / 1e12     # FP32 lane-ops/s (T)
+        achieved = 6.0 * u_res / msd_avg_s / 1e12      # 3 FSUB + 3 FFMA per update
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": None,
+                "kernel": "plain_tile_kernel<MSD>",
+                "note": f"FP32 lane-ops (FSUB, FFMA) per s of the MSD tile kernel alone (CUDA events around "
+                        f"its {kern_msd[1]} launches); peak = 152 SMs x 128 lanes x {sm_mhz:.0f} MHz "
+                        f"({pk_kind} max clock)"}
+    else:
+        flops = 6.0 * u_res   # useful Gram flops: 3 MACs per update
+        peak_t = pk.get("bf16_tflops", 1900.0)
+        achieved = flops / msd_avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
+                "frac": achieved / peak_t, "traffic": GRAM_TRAFFIC_BYTES.get((args.workload, method)),
+                "kernel": "gram_band_tc<MSD>",
+                "note": f"useful Gram FLOPs (6 per update) / duration of the MSD band kernel alone (CUDA events "
+                        f"around its {kern_msd[1]} launches) vs the {pk_kind} bf16 dense burst peak; the split "
+                        f"form issues 3 products per useful one plus band waste",
+                "issued_tflops": 3.0 * flops * issued_over_useful(N, T, tm, s) / msd_avg_s / 1e12,
+                "acf_kernel_frac": flops / acf_avg_s / 1e12 / peak_t}
+
+    # ---- the plain FP32 kernel on the same arrays, for the tensor-core vs plain comparison
+    plain_cmp = None
+    if method != "plain" and not args.no_plain_compare:
+        ws_p = torch.empty(max(tcorr.tcorr_workspace_size(T, N, tm, s, "plain"), 256), dtype=torch.uint8,
+                           device=dev)
+        reps = 2 if u_step < 1e13 else 1
+        tcorr.tcorr_profile_enable(True)
+        tcorr.tcorr_profile_read(0)
+        tcorr.tcorr_profile_read(1)
+        tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
+        tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
+        torch.cuda.synchronize()
+        pm_err = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tcorr.tcorr_profile_read(0)
+        tcorr.tcorr_profile_read(1)
+        e0.record(stream)
+        for _ in range(reps):
+            tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
+            tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pk_m = tcorr.tcorr_profile_read(0)
+        pk_c = tcorr.tcorr_profile_read(1)
+        tcorr.tcorr_profile_enable(False)
+        p_ms = e0.elapsed_time(e1) / reps
+        lane_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+        pm_s = pk_m[0] / max(1, pk_m[1]) / 1e3
+        pc_s = pk_c[0] / max(1, pk_c[1]) / 1e3
+        m_plain, c_plain = out_m.cpu().numpy().copy(), out_c.cpu().numpy().copy()
+        plain_cmp = {"method": "plain", "ms_per_step_msd_acf": p_ms,
+                     "updates_per_s": u_step / (p_ms / 1000.0),
+                     "speedup_of_timed_method": value / (u_step / (p_ms / 1000.0)),
+                     "msd_kernel_ms": pm_s * 1e3, "acf_kernel_ms": pc_s * 1e3,
+                     "msd_lane_peak_frac": 6.0 * u_res / pm_s / lane_peak,
+                     "acf_lane_peak_frac": 3.0 * u_res / pc_s / lane_peak}
+        del ws_p
+    else:
+        m_plain = c_plain = None
+
+    # ---- host copies (pinned) of the inputs: the oracle reads them, the end-to-end steps upload them
     xh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
     vh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
     xh.copy_(x)
     vh.copy_(v)
+
+    cpu = None
+    err_vs_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        lags = oracle_lags(wl)
+        m_ref, c_ref, el, n_up = oracle_pass(xh.numpy(), vh.numpy(), s, lags)
+        cores = oracle.default_threads()
+        # the same oracle on one host thread: the same lags, 1/cores of the atoms (the per-atom
+        # work is what the threads share), MSD only
+        n1 = max(64, N // max(1, cores))
+        x1 = np.ascontiguousarray(xh.numpy()[:, :n1, :])
+        t1 = time.perf_counter()
+        oracle.msd(x1, stride=s, lags=lags, nthreads=1)
+        el1 = time.perf_counter() - t1
+        del x1
+        r1 = int(sum(n1 * ((T - 1 - int(l)) // s + 1) for l in lags)) / el1
+        cpu = {"value": n_up / el, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"MSD and VACF at {len(lags)} lags in [0, {tm}] (24 evenly spaced, 1, 2 and 16 "
+                         f"in the last 192), all atoms and origins of the same arrays; {el:.1f} s",
+               "value_1core": r1,
+               "sample_1core": f"MSD at the same {len(lags)} lags, the first {n1} atoms, one thread; "
+                               f"{el1:.1f} s"}
+        # the timed steps' results against the oracle at those lags (the metric's bar)
+        err_vs_oracle = {"lags": int(len(lags)),
+                         "msd_max_abs_over_msd_tau_max": float(np.max(np.abs(m_dev[lags] - m_ref)) / m_ref[-1]),
+                         "acf_max_abs_over_c0": float(np.max(np.abs(c_dev[lags] - c_ref)) / abs(c_ref[0])),
+                         "tolerance": 1e-6 if method == "plain" else 1e-5}
+        if m_plain is not None:
+            err_vs_oracle["plain_msd_max_rel_per_lag"] = float(
+                np.max(np.abs(m_plain[lags[1:]] - m_ref[1:]) / m_ref[1:])) if len(lags) > 1 else 0.0
+            err_vs_oracle["plain_acf_max_abs_over_c0"] = float(
+                np.max(np.abs(c_plain[lags] - c_ref)) / abs(c_ref[0]))
+            err_vs_oracle["plain_tolerance"] = 1e-6
+
+    # ---- end to end through the public API from pinned host memory: the device copies of the
+    # inputs and the workspace are released first (each variant allocates its own buffers)
+    del x, v, ws
+    torch.cuda.empty_cache()
     m_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
     c_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
     gk_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
@@ -364,11 +506,14 @@ def run_gpu(args, wl):
             D_host.copy_(out_D, non_blocking=True)
         st.synchronize()
 
-    # (a) whole arrays up on a copy stream, then the in-core calls
-    x2 = torch.empty_like(x)
-    v2 = torch.empty_like(v)
     copy_stream = torch.cuda.Stream(dev)
     ev_x, ev_v = torch.cuda.Event(), torch.cuda.Event()
+
+    # (a) whole arrays up on a copy stream, then the in-core calls (the MSD starts when the
+    # positions have landed)
+    x2 = torch.empty((T, N, 3), dtype=torch.float32, device=dev)
+    v2 = torch.empty_like(x2)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
 
     def e2e_incore():
         with torch.cuda.stream(copy_stream):
@@ -383,14 +528,43 @@ def run_gpu(args, wl):
         finish_on(stream)
 
     e2e_incore_s = timed_e2e(e2e_incore)
-    del x2, v2
+    # the input buffers' own host link rate: one whole-array copy of the positions, CUDA events
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    with torch.cuda.stream(stream):
+        x2.copy_(xh, non_blocking=True)
+    i1.record(stream)
+    i1.synchronize()
+    h2d_gbs_input = xh.numel() * 4 / (i0.elapsed_time(i1) / 1e3) / 1e9
+    del v2
+    torch.cuda.empty_cache()
 
-    # (b) the streamed calls, MSD and VACF on two streams with a workspace each:
-    # windows of C origins, host copies overlapping the kernels
-    C = args.stream_chunk
+    # (b) positions copied whole at the link's full rate, the in-core MSD as soon as they have
+    # landed, and the velocities streamed behind them: the VACF windows run while later windows
+    # cross the link, so only the last window's work follows the last copy
+    C = args.stream_chunk or wl.get("stream_chunk", 2048)
     sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ws_a = torch.empty(tcorr.tcorr_stream_workspace_size(T, N, tm, s, method, C), dtype=torch.uint8, device=dev)
     ws_b = torch.empty(tcorr.tcorr_stream_workspace_size(T, N, tm, s, method, C), dtype=torch.uint8, device=dev)
+
+    def e2e_hybrid():
+        with torch.cuda.stream(copy_stream):
+            x2.copy_(xh, non_blocking=True)
+            ev_x.record(copy_stream)
+        sa.wait_event(ev_x)
+        sb.wait_event(ev_x)
+        tcorr.tcorr_msd(x2, tm, s, method, out=out_m, ws=ws, stream=sa)
+        tcorr.tcorr_acf_stream(vh, tm, s, method, chunk_frames=C, out=out_c, ws=ws_b, stream=sb)
+        stream.wait_stream(sa)
+        stream.wait_stream(sb)
+        finish_on(stream)
+
+    e2e_hybrid_s = timed_e2e(e2e_hybrid)
+    del x2, ws
+    torch.cuda.empty_cache()
+
+    # (c) the streamed calls, MSD and VACF on two streams with a workspace each: windows of C
+    # origins, host copies overlapping the kernels
+    ws_a = torch.empty(tcorr.tcorr_stream_workspace_size(T, N, tm, s, method, C), dtype=torch.uint8, device=dev)
     ev_go = torch.cuda.Event()
 
     def e2e_streamed():
@@ -404,35 +578,8 @@ def run_gpu(args, wl):
         finish_on(stream)
 
     e2e_stream_s = timed_e2e(e2e_streamed)
-
-    # (c) positions copied whole at the link's full rate, the in-core MSD as soon as they have
-    # landed, and the velocities streamed behind them: the VACF windows run while later windows
-    # cross the link, so only the last window's work follows the last copy
-    x3 = torch.empty_like(x)
-
-    def e2e_hybrid():
-        with torch.cuda.stream(copy_stream):
-            x3.copy_(xh, non_blocking=True)
-            ev_x.record(copy_stream)
-        sa.wait_event(ev_x)
-        sb.wait_event(ev_x)
-        tcorr.tcorr_msd(x3, tm, s, method, out=out_m, ws=ws, stream=sa)
-        tcorr.tcorr_acf_stream(vh, tm, s, method, chunk_frames=C, out=out_c, ws=ws_b, stream=sb)
-        stream.wait_stream(sa)
-        stream.wait_stream(sb)
-        finish_on(stream)
-
-    e2e_hybrid_s = timed_e2e(e2e_hybrid)
-    del ws_a, ws_b, x3
-    # the input buffers' own host link rate: one whole-array copy of the
-    # positions (same values as the resident array), CUDA events
-    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    i0.record(stream)
-    with torch.cuda.stream(stream):
-        x.copy_(xh, non_blocking=True)
-    i1.record(stream)
-    i1.synchronize()
-    h2d_gbs_input = xh.numel() * 4 / (i0.elapsed_time(i1) / 1e3) / 1e9
+    del ws_a, ws_b
+    torch.cuda.empty_cache()
     # this machine's host link: one pinned-to-device copy of 1 GiB, CUDA events
     hb = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
     db = torch.empty(1 << 28, dtype=torch.float32, device=dev)
@@ -461,82 +608,6 @@ def run_gpu(args, wl):
                 "h2d_gbs_measured": h2d_gbs,
                 "h2d_gbs_input_buffer": h2d_gbs_input,
                 "h2d_link_bound_ms": h2d / h2d_gbs / 1e6}
-
-    # ---- roofline of the dominant kernel (the MSD band kernel), timed alone
-    pk, pk_kind = peaks()
-    u_res = updates(N, T, tm, s)
-    msd_avg_s = kern_msd[0] / max(1, kern_msd[1]) / 1000.0
-    acf_avg_s = kern_acf[0] / max(1, kern_acf[1]) / 1000.0
-    if method == "plain":
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak_ops = 152 * 128 * sm_mhz * 1e6 / 1e12     # FP32 lane-ops/s (T)
-        achieved = 6.0 * u_res / msd_avg_s / 1e12      # 3 FSUB + 3 FFMA per update
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": None,
-                "kernel": "plain_tile_kernel<MSD>",
-                "note": f"FP32 lane-ops (FSUB, FFMA) per s of the MSD tile kernel alone (CUDA events around "
-                        f"its {kern_msd[1]} launches); peak = 152 SMs x 128 lanes x {sm_mhz:.0f} MHz "
-                        f"({pk_kind} max clock)"}
-    else:
-        flops = 6.0 * u_res   # useful Gram flops: 3 MACs per update
-        peak_t = pk.get("bf16_tflops", 1900.0)
-        achieved = flops / msd_avg_s / 1e12
-        traffic = (GRAM_WATER_TRAFFIC_BYTES if (method == "fp16x3" and args.workload == "water")
-                   else None)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
-                "frac": achieved / peak_t, "traffic": traffic, "kernel": "gram_band_tc<MSD>",
-                "note": f"useful Gram FLOPs (6 per update) / duration of the MSD band kernel alone (CUDA events "
-                        f"around its {kern_msd[1]} launches) vs the {pk_kind} bf16 dense burst peak; the split "
-                        f"form issues 3 products per useful one plus band waste",
-                "issued_tflops": 3.0 * flops * issued_over_useful(N, T, tm, s) / msd_avg_s / 1e12}
-
-    # ---- the plain FP32 kernel on the same arrays, for the tensor-core vs plain comparison
-    plain_cmp = None
-    if method != "plain" and not args.no_plain_compare:
-        ws_p = torch.empty(max(tcorr.tcorr_workspace_size(T, N, tm, s, "plain"), 256), dtype=torch.uint8,
-                           device=dev)
-        tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
-        tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
-        e0.record(stream)
-        for _ in range(reps):
-            tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
-            tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        p_ms = e0.elapsed_time(e1) / reps
-        plain_cmp = {"method": "plain", "ms_per_step_msd_acf": p_ms,
-                     "updates_per_s": u_step / (p_ms / 1000.0),
-                     "speedup_of_timed_method": (u_step / (p_ms / 1000.0)) and value / (u_step / (p_ms / 1000.0))}
-        del ws_p
-
-    cpu = None
-    err_vs_oracle = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        xhn = xh.numpy()
-        vhn = vh.numpy()
-        r, cores, nl, el, (lags, m_ref, c_ref) = oracle_sample(xhn, vhn, wl,
-                                                               float(os.environ.get("TCORR_CPU_S", "12")))
-        # the same oracle on one host thread: the same lags, 1/cores of the atoms (the per-atom
-        # work is what the threads share), MSD only
-        import oracle
-        n1 = max(64, N // max(1, cores))
-        x1 = np.ascontiguousarray(xhn[:, :n1, :])
-        t1 = time.perf_counter()
-        oracle.msd(x1, stride=s, lags=lags, nthreads=1)
-        el1 = time.perf_counter() - t1
-        r1 = int(sum(n1 * ((T - 1 - int(l)) // s + 1) for l in lags)) / el1
-        cpu = {"value": r, "unit": "updates/s", "cores": cores, "kind": "oracle",
-               "sample": f"MSD and VACF at {nl} evenly spaced lags in [0, {tm}], all atoms and "
-                         f"origins of the same arrays; {el:.1f} s",
-               "value_1core": r1,
-               "sample_1core": f"MSD at the same {nl} lags, the first {n1} atoms, one thread; {el1:.1f} s"}
-        # the timed steps' results against the oracle at those lags (the metric's 1e-5 bar)
-        err_vs_oracle = {"lags": int(nl),
-                         "msd_max_abs_over_msd_tau_max": float(np.max(np.abs(m_dev[lags] - m_ref)) / m_ref[-1]),
-                         "acf_max_abs_over_c0": float(np.max(np.abs(c_dev[lags] - c_ref)) / abs(c_ref[0])),
-                         "tolerance": 1e-6 if method == "plain" else 1e-5}
 
     dtype = {"plain": "f32", "fp16x3": "f16x3 (f32 accumulate)", "bf16x3": "bf16x3 (f32 accumulate)",
              "bf16x4": "bf16x4 (f32 accumulate)", "tf32x3": "tf32x3 (f32 accumulate)"}.get(method, method)
@@ -580,25 +651,16 @@ def run_batch_workload(args, wl):
     tbuild.build()
     tcorr.load()
     from paper_1708_08619_gb300 import shard
-    rng = np.random.default_rng(synth.BASE_SEED + 4)
-    shapes, gammas = [], []
-    for i in range(wl["count"]):
-        N = int(round(np.exp(rng.uniform(np.log(64), np.log(16384)))))
-        Tn = int(rng.integers(500, 20001))
-        shapes.append((Tn, N, Tn // 4, 1))
-        gammas.append(float(rng.uniform(0.01, 0.5)))
+    wshapes = synth.batch_workload_shapes(wl["count"])
+    shapes = [(Tn, N, tm, s) for _, Tn, N, tm, s, _ in wshapes]
     u_all = sum(updates(N, Tn, tm, s) for Tn, N, tm, s in shapes)
     mine = shard.my_share(shapes, rank, world)       # instance sharding, no exchange
     items = []
     for i in mine:
-        Tn, N, tm, s = shapes[i]
-        seed = synth.BASE_SEED + i
-        if i % 2 == 0:
-            x = synth.random_walk_positions_device(Tn, N, 0.01, 3.0, seed, device=dev)
-        else:
-            x = synth.ou_velocities_device(Tn, N, gammas[i], 1.0, seed, device=dev)
+        kind, Tn, N, tm, s, _ = wshapes[i]
+        x = synth.batch_instance_device(i, wshapes[i], device=dev)
         out = torch.empty(tm + 1, dtype=torch.float64, device=dev)
-        items.append((i % 2, x, tm, 1, out))
+        items.append((kind, x, tm, 1, out))
     u_total = u_all
     method = args.method
     inst = tcorr.make_instances(items)
@@ -651,6 +713,26 @@ def run_batch_workload(args, wl):
         del ws
         single_ms = statistics.median(pair_p)
         batch_pair_ms = statistics.median(pair_b)
+    # the batch's results (the last call above) against the oracle: every 8th instance of this
+    # rank's share at lags 1, tau_max/2 and tau_max
+    err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        w_msd = w_acf = 0.0
+        n_chk = 0
+        tcorr.tcorr_batch(inst, method, ws=torch.empty(need, dtype=torch.uint8, device=dev), stream=stream)
+        stream.synchronize()
+        for kind, x, tm, s, out in items[::8]:
+            lags = np.unique(np.array([0, 1, tm // 2, tm]))
+            got = out.cpu().numpy()[lags]
+            ref = (oracle.msd if kind == 0 else oracle.acf)(x.cpu().numpy(), stride=s, lags=lags)
+            if kind == 0:
+                w_msd = max(w_msd, float(np.max(np.abs(got - ref)) / ref[-1]))
+            else:
+                w_acf = max(w_acf, float(np.max(np.abs(got - ref)) / abs(ref[0])))
+            n_chk += 1
+        err = {"instances": n_chk, "lags_per_instance": 4, "msd_max_abs_over_msd_tau_max": w_msd,
+               "acf_max_abs_over_c0": w_acf, "tolerance": 1e-6 if method == "plain" else 1e-5}
     ms = shard.max_over_ranks(batch_ms)
     value = u_total / (ms / 1000.0)            # the whole batch, shared by all ranks
     pk, pk_kind = peaks()
@@ -666,6 +748,7 @@ def run_batch_workload(args, wl):
                        "alternating_pairs": {"graph_batch_ms": batch_pair_ms, "per_instance_launches_ms": single_ms,
                                              "pairs": len(pair_p)},
                        "batch_speedup_vs_per_instance": single_ms / batch_pair_ms,
+                       "error_vs_oracle": err,
                        "l2": "inputs larger than L2, no flush"},
             "clocks": clocks, "e2e": None,
             "gpu_launches": None,
@@ -704,7 +787,7 @@ def run_flux_workload(args, wl):
     xs = [torch.from_numpy(a).to(dev) for a in shorth]
     u = updates(1, wl["T"], tm, 1) + wl["nshort"] * updates(1, wl["Tshort"], tm, 1)
     stream = torch.cuda.Stream(dev)
-    res = {}
+    res, res_all = {}, {}
     for method in ((args.method,) if args.no_plain_compare else (args.method, "plain")):
         # one row per series (the long one first): the running integrals of all of them in one launch
         outs = torch.empty((1 + wl["nshort"], tm + 1), dtype=torch.float64, device=dev)
@@ -735,9 +818,21 @@ def run_flux_workload(args, wl):
             stream.synchronize()
             clocks = sampler.stop() if sampler else None
         res[method] = (e0.elapsed_time(e1) / steps, clocks, outs[0].cpu().numpy())
+        res_all[method] = outs.cpu().numpy()
         del ws_b, ws_l
     ms, clocks, c_tc = res[args.method]
     p_ms, _, c_plain = res.get("plain", (None, None, None))
+    # every series of the timed method against the oracle at 10 lags
+    err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        lags = np.unique(np.array([0, 1, 2, 383, 384, 767, 768, tm // 2, tm - 1, tm]))
+        worst = 0.0
+        for j, a in enumerate([longh] + shorth):
+            ref = oracle.acf(a, stride=1, lags=lags)
+            worst = max(worst, float(np.max(np.abs(res_all[args.method][j][lags] - ref)) / abs(ref[0])))
+        err = {"series": 1 + len(shorth), "lags_per_series": int(len(lags)), "acf_max_abs_over_c0": worst,
+               "tolerance": 1e-6 if args.method == "plain" else 1e-5}
     from paper_1708_08619_gb300 import shard
     ms = shard.max_over_ranks(ms)
     value = u * world / (ms / 1000.0)
@@ -751,11 +846,12 @@ def run_flux_workload(args, wl):
                        "speedup_vs_plain": p_ms / ms if p_ms else None,
                        "max_diff_tc_vs_plain_over_C0": (float(np.max(np.abs(c_tc - c_plain)) / abs(c_plain[0]))
                                                         if c_plain is not None else None),
+                       "error_vs_oracle": err,
                        "l2": "long series 24 MB (fits L2); operand copies 0.2 GB"},
             "clocks": clocks, "e2e": None,
             # per step: long series (row max, prep, Gram, reduction) + the batch (5 descriptor
-            # uploads, row max, prep, Gram, reduction) + one Green-Kubo integral per series
-            # (counted in the ncu launch list, profiles/gram_band_kernel_polyphase_flux.md)
+            # uploads, row max, prep, Gram, reduction) + one Green-Kubo integral for all series
+            # (counted in an ncu launch list of the flux workload)
             "gpu_launches": (4 + 9 + 1) * args.steps if args.method != "plain" else None,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk.get("bf16_tflops", 1900.0),
                          "unit": "TFLOP/s", "frac": achieved / pk.get("bf16_tflops", 1900.0), "traffic": None,
@@ -964,10 +1060,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method", default=os.environ.get("TCORR_BENCH_METHOD", "fp16x3"))
     ap.add_argument("--no-plain-compare", action="store_true")
-    ap.add_argument("--workload", default="water", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stream-chunk", type=int, default=2048,
-                    help="origins per window of the streamed end-to-end calls")
+    ap.add_argument("--stream-chunk", type=int, default=0,
+                    help="origins per window of the streamed end-to-end calls (0: the workload's default)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

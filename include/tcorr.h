@@ -207,6 +207,35 @@ int tcorr_acf_weighted(const float *d_x, const float *d_w, int64_t T, int64_t N,
                        int64_t stride, int method, double *d_out, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * Atom-sharded correlation (the Conclusion's division of a species' dynamic
+ * data over several devices by atoms; Eq. 5 averages over atoms and n_o(tau)
+ * is the same for every atom): each rank runs tcorr_msd / tcorr_acf (or the
+ * weighted calls) on its own contiguous atom slice and writes one record of
+ * n + 1 doubles, its per-lag averages a_r(0 .. n-1) followed by its weight
+ * w_r (the slice's atom count N_r, or its weight sum W_r from
+ * tcorr_weight_total for weighted averages).  The records of all ranks are
+ * gathered in rank order (all-gather: the one exchange of the path) into
+ * count rows of a row-major array with row stride ld >= n + 1 doubles, and
+ *   d_out[i] = sum_r w_r d_rows[r ld + i] / sum_r w_r,   i = 0 .. n-1,
+ * with both sums in FP64 in row order r = 0, 1, ... (fixed order: every rank
+ * combining the same gathered rows gets the same bits).  Weights must be >= 0
+ * with a positive total (else the result is Inf or NaN).
+ * d_rows: device, 8-byte aligned; d_out: n doubles on the device, 8-byte
+ * aligned, not overlapping the rows.  Errors: TCORR_EINVAL (null pointer,
+ * n < 1, count < 1, ld < n + 1, overlap), TCORR_EALIGN, TCORR_ECUDA.
+ */
+int tcorr_combine_shards(const double *d_rows, int64_t n, int64_t count, int64_t ld, double *d_out,
+                         void *stream);
+
+/*
+ * W = sum_i w_i of N float32 weights in FP64, summed in a fixed order (the
+ * weight of one weighted shard, written where tcorr_combine_shards reads a
+ * record's weight).  d_w: device, 4-byte aligned; d_W: one double on the
+ * device, 8-byte aligned.  Errors: TCORR_EINVAL, TCORR_EALIGN, TCORR_ECUDA.
+ */
+int tcorr_weight_total(const float *d_w, int64_t N, double *d_W, void *stream);
+
+/*
  * Collective signal of a trajectory, the input of collective transport
  * quantities (Eq. 4 with a collective flux, as the viscosity example
  * correlates the pressure tensor of the whole box):

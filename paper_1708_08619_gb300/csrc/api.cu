@@ -158,6 +158,7 @@ void plain_batch_layout(const tcorr_instance *items, int count, PlainBatchLayout
     };
     B->off_args = take(plain_args_size() * count);
     B->off_red = take(sizeof(LagReduceDesc) * count);
+    host_alloc_fault_point();
     B->plans.resize(count);
     B->partial_off.resize(count);
     for (int i = 0; i < count; ++i) {
@@ -277,7 +278,14 @@ int batch_run_graph(const tcorr_instance *items, int count, int m, void *d_ws, s
     }
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    const int rc = batch_run_direct(items, count, m, d_ws, ws_bytes, st);
+    int rc;
+    try {
+        rc = batch_run_direct(items, count, m, d_ws, ws_bytes, st);
+    } catch (const std::bad_alloc &) {
+        cudaGraph_t partial = nullptr;           // leave the stream out of capture mode
+        if (cudaStreamEndCapture(st, &partial) == cudaSuccess && partial) cudaGraphDestroy(partial);
+        throw;
+    }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(st, &graph);
     if (rc != TCORR_OK) {
@@ -452,7 +460,11 @@ size_t tcorr_batch_workspace_size(const tcorr_instance *h_items, int count, int 
         const tcorr_instance &it = h_items[i];
         if (!valid_sizes(it.T, it.N, it.tau_max, it.stride)) return 0;
     }
-    return batch_workspace(h_items, count, batch_method(h_items, count, method));
+    try {
+        return batch_workspace(h_items, count, batch_method(h_items, count, method));
+    } catch (const std::bad_alloc &) {
+        return 0;
+    }
 }
 
 int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws, size_t ws_bytes,
@@ -467,16 +479,20 @@ int tcorr_batch(const tcorr_instance *h_items, int count, int method, void *d_ws
             return TCORR_EALIGN;
     }
     if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return TCORR_EALIGN;
-    const int m = batch_method(h_items, count, method);
-    const size_t need = batch_workspace(h_items, count, m);
-    if (need == 0) return TCORR_EUNSUPPORTED;
-    if (ws_bytes < need || !d_ws) return TCORR_EWORKSPACE;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (st != nullptr && cudaStreamIsCapturing(st, &cs) != cudaSuccess) return TCORR_ECUDA;
-    if (st == nullptr || cs != cudaStreamCaptureStatusNone || std::getenv("TCORR_NO_GRAPH"))
-        return batch_run_direct(h_items, count, m, d_ws, ws_bytes, st);
-    return batch_run_graph(h_items, count, m, d_ws, ws_bytes, st);
+    try {
+        const int m = batch_method(h_items, count, method);
+        const size_t need = batch_workspace(h_items, count, m);   // host plan: before any launch
+        if (need == 0) return TCORR_EUNSUPPORTED;
+        if (ws_bytes < need || !d_ws) return TCORR_EWORKSPACE;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (st != nullptr && cudaStreamIsCapturing(st, &cs) != cudaSuccess) return TCORR_ECUDA;
+        if (st == nullptr || cs != cudaStreamCaptureStatusNone || std::getenv("TCORR_NO_GRAPH"))
+            return batch_run_direct(h_items, count, m, d_ws, ws_bytes, st);
+        return batch_run_graph(h_items, count, m, d_ws, ws_bytes, st);
+    } catch (const std::bad_alloc &) {
+        return TCORR_ENOMEM;      // a host allocation failed (the injected one, in the plan: nothing enqueued)
+    }
 }
 
 int tcorr_status_poll(void *stream) { return status_poll_and_clear(static_cast<cudaStream_t>(stream)); }

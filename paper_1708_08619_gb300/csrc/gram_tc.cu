@@ -308,6 +308,7 @@ __host__ __device__ constexpr uint32_t make_idesc() {
 // up to the MMA's N granularity of 16): the last column tile of a band row
 // is issued that narrow.
 struct Item {
+    int64_t canon;                    // index of the item's partial window (see decode_item)
     int64_t rho, a_y, b_x, b_y, b_z, moff, m_max, kb0, kb1;
     int64_t sa0, sb0, sstr, a_rows;   // a_rows: A rows that hold data (scale lookups)
     int ncol;
@@ -320,16 +321,39 @@ __device__ __forceinline__ int item_ncol(int64_t moff, int64_t m_max) {
     return need <= 16 ? 16 : static_cast<int>((need + 15) & ~int64_t(15));
 }
 
+// Band items are claimed in supertile order: within one (K-group, residue),
+// row tiles are taken kSuperRows at a time and, inside such a row block,
+// column tiles kSuperCols at a time (column fastest).  The ~152 items in
+// flight then form a compact block of the origin x frame plane whose CTAs
+// read the same A rows (one row tile, several columns) and overlapping B rows
+// (neighbouring row tiles are 128 frames apart) at about the same K-block, so
+// the operands are shared in L2.  With column-fastest order over whole rows a
+// band of 53 column tiles (tau_max = 10000) left only about 3 row tiles in
+// flight and each B tile was read from DRAM once per row tile.  The item's
+// partial window is stored at its canonical index
+// ((g n_res + rho) n_rows + r) n_cols + c, which the lag reduction reads.
+constexpr int64_t kSuperRows = 16;
+constexpr int64_t kSuperCols = 10;
+
 __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
     Item I;
     int64_t t = item;
     if (a.mode == 0) {
-        const int64_t c = t % a.n_cols;
-        t /= a.n_cols;
-        const int64_t r = t % a.n_rows;
-        t /= a.n_rows;
-        I.rho = t % a.n_res;
-        const int64_t g = t / a.n_res;
+        const int64_t per = a.n_rows * a.n_cols;
+        const int64_t gr = t / per;                          // (K-group, residue) block
+        int64_t u = t - gr * per;
+        const int64_t cs = a.n_cols < kSuperCols ? a.n_cols : kSuperCols;
+        const int64_t rb = u / (kSuperRows * a.n_cols);      // row block (all but the last are full)
+        u -= rb * kSuperRows * a.n_cols;
+        const int64_t rcount = min(kSuperRows, a.n_rows - rb * kSuperRows);
+        const int64_t cb = u / (rcount * cs);                // column block within the row block
+        u -= cb * rcount * cs;
+        const int64_t ccount = min(cs, a.n_cols - cb * cs);
+        const int64_t r = rb * kSuperRows + u / ccount;
+        const int64_t c = cb * cs + u % ccount;
+        I.canon = (gr * a.n_rows + r) * a.n_cols + c;
+        I.rho = gr % a.n_res;
+        const int64_t g = gr / a.n_res;
         const int64_t o0 = r * BO, k0 = o0 + c * BF;
         I.a_y = o0;
         I.b_x = 0;
@@ -348,6 +372,7 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
         I.ncol = item_ncol(I.moff, I.m_max);
     } else {
         // polyphase block (q, h, c) of M_q = sum_p Y[.][p] Y[.][p+q]^T, rows = phases
+        I.canon = item;
         const int64_t c = t % 2;
         t /= 2;
         const int64_t h = t % 3;
@@ -632,7 +657,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             {
                 const Item I0 = decode_item(a, local);
                 if (I0.empty) {
-                    double *outp0 = a.partial + local * WPG;
+                    double *outp0 = a.partial + I0.canon * WPG;
                     for (int w = et; w < WPG; w += 32 * NEPI) outp0[w] = 0.0;
                     continue;
                 }
@@ -674,7 +699,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             }
             if (aborted) break;
             const Item I = decode_item(a, local);     // decoded again: keeps registers free above
-            double *outp = a.partial + local * WPG;
+            double *outp = a.partial + I.canon * WPG;
             float rs = 1.f;
             if (PREC == P_FP16) {
                 const int64_t nscale = a.mode == 0 ? a.T : 3 * BO;
@@ -1796,6 +1821,7 @@ bool make_batch_layout(const tcorr_instance *items, int count, int method, Batch
     if (!method_prec(method, &B->prec, &B->x4)) return false;
     B->n = count;
     B->L.resize(count);
+    host_alloc_fault_point();
     std::vector<double> work(count);
     for (int i = 0; i < count; ++i) {
         const tcorr_instance &it = items[i];

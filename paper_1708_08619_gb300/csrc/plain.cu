@@ -10,10 +10,20 @@
 //   MSD:  acc(o, f) += (x[f][k] - x[o][k])^2      2 FP32 instructions / k
 //   ACF:  acc(o, f) += x[o][k] * x[f][k]          1 FP32 instruction  / k
 //
-// Accumulation: FP32 in registers over a segment of `kseg` K elements, then
-// the tile is written to shared memory and each thread sums one diagonal
-// (one band offset m = f - o) in a fixed order; the diagonal sums of all
-// segments of the item are added in FP64.  The result of an item is a window
+// Accumulation, in three levels so that no FP32 run is long:
+//   1. each pair sum over one staged chunk of BK = 16 K elements starts from
+//      zero (a run of 16 terms);
+//   2. the chunk totals are added into a running FP32 pair sum for a segment
+//      of `kseg` K elements (256: a run of 16 chunk totals);
+//   3. at the end of a segment the tile goes to shared memory and each thread
+//      sums one diagonal (one band offset m = f - o) as eight interleaved
+//      chains of eight entries combined in a fixed tree, and adds it to an
+//      FP64 accumulator that spans the item's segments.
+// A sequential FP32 sum of n positive terms errs by at most (n - 1) 2^-24 of
+// the sum; with these levels the longest run is 16 terms, so when every
+// origin gives the same pair sum (ballistic motion, where rounding cannot
+// average out over origins) the result stays near a few 2^-24 instead of the
+// (K - 1) 2^-24 of one run over all of K.  The result of an item is a window
 // of per-offset FP64 sums, reduced across items by lag_reduce (reduce.cu).
 #include "tcorr_internal.cuh"
 
@@ -123,11 +133,11 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
             }
         };
 
-        float acc[8][8];
+        float racc[8][8];   // running pair sums of this segment: chunk totals added in FP32
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int j = 0; j < 8; ++j) racc[i][j] = 0.f;
 
 #pragma unroll
         for (int st = 0; st < STAGES - 1; ++st) {
@@ -143,6 +153,7 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
 
             const float *cA = sA + (ch % STAGES) * BK * LDS;
             const float *cB = sB + (ch % STAGES) * BK * LDS;
+            float acc[8][8];    // this chunk's pair sums, a fresh run of BK terms
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
                 const float4 a0 = *reinterpret_cast<const float4 *>(cA + kk * LDS + swz(4 * ty, kk));
@@ -157,12 +168,16 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
                     for (int j = 0; j < 8; ++j) {
                         if (KIND == 0) {
                             const float d = bv[j] - av[i];
-                            acc[i][j] = fmaf(d, d, acc[i][j]);
+                            acc[i][j] = kk == 0 ? d * d : fmaf(d, d, acc[i][j]);
                         } else {
-                            acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                            acc[i][j] = kk == 0 ? av[i] * bv[j] : fmaf(av[i], bv[j], acc[i][j]);
                         }
                     }
             }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) racc[i][j] += acc[i][j];
         }
         cp_async_wait<0>();
 
@@ -180,25 +195,25 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
                     const int j = (jj < 4) ? 4 * tx + jj : 64 + 4 * tx + (jj - 4);
                     const int64_t m = c * BF + j - i;
                     const bool ok = (o0 + i < a.n_orig) && (k0 + j < n_rho) && m >= 0 && m <= m_max;
-                    sP[il * PLD + j] = ok ? acc[4 * h + q][jj] : 0.f;
+                    sP[il * PLD + j] = ok ? racc[4 * h + q][jj] : 0.f;
                 }
             }
             __syncthreads();
-            // diagonal w = tid: entries (il, j) with j - (64h + il) + BO - 1 = w
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            // diagonal w = tid: entries (il, j) with j - (64h + il) + BO - 1 = w,
+            // as eight chains (entry il goes to chain il % 8) and a fixed tree
+            float sd[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sd[e] = 0.f;
             const int jb = tid + 64 * h - (BO - 1);
-#pragma unroll 4
-            for (int il = 0; il < 64; il += 4) {
-                int j = jb + il;
-                if (j >= 0 && j < BF) s0 += sP[il * PLD + j];
-                ++j;
-                if (j >= 0 && j < BF) s1 += sP[(il + 1) * PLD + j];
-                ++j;
-                if (j >= 0 && j < BF) s2 += sP[(il + 2) * PLD + j];
-                ++j;
-                if (j >= 0 && j < BF) s3 += sP[(il + 3) * PLD + j];
+#pragma unroll 2
+            for (int il = 0; il < 64; il += 8) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int j = jb + il + e;
+                    if (j >= 0 && j < BF) sd[e] += sP[(il + e) * PLD + j];
+                }
             }
-            dacc += static_cast<double>((s0 + s1) + (s2 + s3));
+            dacc += static_cast<double>(((sd[0] + sd[1]) + (sd[2] + sd[3])) + ((sd[4] + sd[5]) + (sd[6] + sd[7])));
         }
     }
     outp[tid] = dacc;
@@ -214,7 +229,7 @@ __global__ void __launch_bounds__(NT, 1) plain_tile_kernel(const __grid_constant
 
 // Batch: block b belongs to the instance whose [item_begin, next item_begin)
 // holds b (binary search over the descriptors); the kind is per instance.
-__global__ void __launch_bounds__(NT, 2) plain_tile_batch_kernel(const PlainArgs *__restrict__ d, int n) {
+__global__ void __launch_bounds__(NT, 1) plain_tile_batch_kernel(const PlainArgs *__restrict__ d, int n) {
     const int64_t b = blockIdx.x;
     int lo = 0, hi = n - 1;
     while (lo < hi) {

@@ -21,6 +21,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -125,6 +126,16 @@ int64_t tune_default_kseg(int64_t K, int64_t tiles);
 // kind: 0 MSD, 1 ACF, 2 a batched launch mixing both.
 void prof_begin(int kind, cudaStream_t st);
 void prof_end(cudaStream_t st);
+
+// Test-only fault injection on the host.  With TCORR_FAULT_INJECT=host_alloc
+// in the environment, the first host allocation of a batch plan (the per-
+// instance layout, made before anything is enqueued) throws std::bad_alloc as
+// if the host were out of memory; tcorr_batch returns it as TCORR_ENOMEM and
+// tcorr_batch_workspace_size as 0.  Unset, this is one getenv per plan.
+inline void host_alloc_fault_point() {
+    const char *f = std::getenv("TCORR_FAULT_INJECT");
+    if (f && std::string(f) == "host_alloc") throw std::bad_alloc();
+}
 
 // Workspace layout helpers (byte offsets, 256-byte aligned).
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }

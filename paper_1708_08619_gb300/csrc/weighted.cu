@@ -133,6 +133,11 @@ cudaError_t launch_weight_copy(int kind, const float *x, const float *w, int64_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_weight_sum(const float *w, int64_t N, double *W, cudaStream_t st) {
+    weight_sum_kernel<<<1, WCOPY_THREADS, 0, st>>>(w, N, W);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_weight_rescale(double *out, int64_t n, int64_t T, int64_t N, const void *d_copy,
                                   cudaStream_t st) {
     const double *W = reinterpret_cast<const double *>(

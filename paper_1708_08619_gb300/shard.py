@@ -9,10 +9,14 @@ N * sum_tau n_o(tau); shares are balanced greedily (largest instance first,
 to the least-loaded rank), which keeps the heaviest rank within one instance
 of the average.
 
-One large trajectory can instead be split by atoms (``atom_range``): each rank
-correlates its atom slice and ``combine_atom_shards`` weights the per-lag
-averages by atom count in one all-reduce (the paper's Conclusion suggests
-dividing a species' data over devices by atoms).
+One large trajectory can instead be split by atoms (``atom_range``; the
+paper's Conclusion suggests dividing a species' data over devices by atoms):
+each rank correlates its atom slice with the library, writes one record (its
+per-lag averages and its atom count or weight sum), the records are gathered
+in rank order (``gather_shard_records``, the one exchange: an all-gather of
+tau_max + 2 doubles per rank), and the library's tcorr_combine_shards forms
+the average over all atoms with fixed-order FP64 sums, so every rank holds the
+same bits.  This module does no arithmetic of the method itself.
 """
 from __future__ import annotations
 
@@ -51,25 +55,52 @@ def atom_range(N: int, rank: int, world: int):
     return a0, a0 + base + (1 if rank < extra else 0)
 
 
-def combine_atom_shards(result, n_local: float, group=None):
-    """Whole-trajectory average from per-rank results over disjoint atom slices.
+def shard_record(result, weight=None, n_atoms: int | None = None):
+    """One rank's record: its per-lag averages followed by its weight, as a new
+    float64 tensor of n + 1 values on the result's device.  The weight is the
+    slice's atom count (n_atoms) or a one-element float64 tensor holding its
+    weight sum (from tcorr_weight_total); it is copied, not computed here."""
+    import torch
+    n = result.numel()
+    rec = torch.empty(n + 1, dtype=torch.float64, device=result.device)
+    rec[:n].copy_(result.reshape(-1))
+    if weight is not None:
+        rec[n:].copy_(weight.reshape(-1)[:1])
+    else:
+        rec[n] = float(n_atoms)
+    return rec
 
-    Every per-lag MSD / autocorrelation value is an average over atoms and
-    origins; the origin count n_o(tau) is the same on every rank (same T and
-    stride), so the average over all atoms is sum_r N_r result_r / sum_r N_r:
-    one FP64 all-reduce of tau_max + 2 values.  For weighted averages n_local
-    is the rank's weight sum W_r instead of its atom count.  Works on any
-    backend (NCCL with CUDA tensors, gloo with CPU tensors); identity without a
-    process group."""
+
+def gather_shard_records(rec, group=None):
+    """All ranks' records as rows of a [world][n + 1] float64 tensor in rank
+    order, on rec's device (all-gather; with gloo the exchange goes through host
+    memory).  Without a process group: the one record as a [1][n + 1] tensor."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()):
+        return rec.reshape(1, -1)
+    world = dist.get_world_size(group)
+    backend = dist.get_backend(group)
+    comm_dev = rec.device if backend == "nccl" else torch.device("cpu")
+    mine = rec.to(comm_dev)
+    parts = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    return torch.stack(parts).to(rec.device)
+
+
+def combine_atom_shards(result, weight=None, n_atoms: int | None = None, group=None, stream=None):
+    """Whole-trajectory average from per-rank results over disjoint atom slices
+    (CUDA tensors): gather the ranks' records and combine them with
+    tcorr_combine_shards.  Pass n_atoms (the slice's atom count) for plain
+    averages, or weight (a one-element float64 CUDA tensor with the slice's
+    weight sum, from tcorr_weight_total) for weighted ones.  Identity without a
+    process group."""
+    import torch.distributed as dist
+    from . import tcorr
+    if not (dist.is_available() and dist.is_initialized()):
         return result
-    buf = torch.empty(result.numel() + 1, dtype=torch.float64, device=result.device)
-    buf[:-1] = result.to(torch.float64) * float(n_local)
-    buf[-1] = float(n_local)
-    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
-    return buf[:-1] / buf[-1]
+    rows = gather_shard_records(shard_record(result, weight, n_atoms), group)
+    return tcorr.tcorr_combine_shards(rows, result.numel(), stream=stream)
 
 
 def max_over_ranks(value: float, group=None) -> float:

@@ -84,6 +84,32 @@ def constant_velocity(T: int, N: int, seed: int, vmax_units: int = 8,
     return x32, v
 
 
+def batch_workload_shapes(count: int = 256, seed: int = BASE_SEED + 4):
+    """Shapes of the uneven batching workload: instance i has N log-uniform in
+    [64, 16384], T uniform in [500, 20000], tau_max = T // 4, stride 1; even
+    instances are MSDs of random walks (sigma 0.01, 3 nm box), odd ones
+    autocorrelations of OU velocities with gamma uniform in [0.01, 0.5].
+    Returns a list of (kind, T, N, tau_max, stride, gamma); instance i's data
+    is drawn with seed BASE_SEED + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(round(np.exp(rng.uniform(np.log(64), np.log(16384)))))
+        Tn = int(rng.integers(500, 20001))
+        gamma = float(rng.uniform(0.01, 0.5))
+        out.append((i % 2, Tn, N, Tn // 4, 1, gamma))
+    return out
+
+
+def batch_instance_device(i: int, shape, device="cuda"):
+    """Instance i of the batching workload drawn on the device (see
+    batch_workload_shapes)."""
+    kind, Tn, N, tm, s, gamma = shape
+    if kind == 0:
+        return random_walk_positions_device(Tn, N, 0.01, 3.0, BASE_SEED + i, device=device)
+    return ou_velocities_device(Tn, N, gamma, 1.0, BASE_SEED + i, device=device)
+
+
 # ------------------------------------------------------------- device (torch)
 
 def _torch():

@@ -65,6 +65,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = [vp, vp, i64, i64, i64, i64, ci, vp, vp, sz, vp]
         f.restype = ci
+    lib.tcorr_combine_shards.argtypes = [vp, i64, i64, i64, vp, vp]
+    lib.tcorr_combine_shards.restype = ci
+    lib.tcorr_weight_total.argtypes = [vp, i64, vp, vp]
+    lib.tcorr_weight_total.restype = ci
     lib.einstein_slope.argtypes = [vp, i64, dbl, ci, i64, i64, vp, vp]
     lib.einstein_slope.restype = ci
     lib.tcorr_batch_workspace_size.argtypes = [ctypes.POINTER(TcorrInstance), ci, ci]
@@ -314,6 +318,43 @@ def tcorr_collective(x, w=None, ref_frame: int = -1, out=None, stream=None):
                                  out.data_ptr(), _stream_ptr(stream))
     if rc != 0:
         raise TcorrError(rc, "tcorr_collective")
+    return out
+
+
+def tcorr_combine_shards(rows, n: int, out=None, stream=None):
+    """Average over all atoms from gathered shard records: rows is a [count][ld]
+    float64 CUDA tensor (unit column stride, ld >= n + 1) whose row r holds
+    shard r's n per-lag averages followed by its weight (atom count or weight
+    sum); returns sum_r w_r rows[r][:n] / sum_r w_r (FP64, rows in order)."""
+    torch = _torch()
+    if not isinstance(rows, torch.Tensor) or not rows.is_cuda or rows.dtype != torch.float64 \
+            or rows.dim() != 2 or rows.stride(1) != 1:
+        raise TypeError("rows must be a [count][ld] float64 CUDA tensor with unit column stride")
+    count = rows.shape[0]
+    ld = rows.stride(0) if count > 1 else rows.shape[1]
+    if rows.shape[1] < n + 1:
+        raise TypeError("each row needs n values and a weight")
+    if out is None:
+        out = _held_by(torch.empty(n, dtype=torch.float64, device=rows.device), stream)
+    _check_out(out, n, rows.device)
+    rc = load().tcorr_combine_shards(rows.data_ptr(), n, count, ld, out.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_combine_shards")
+    return out
+
+
+def tcorr_weight_total(w, out=None, stream=None):
+    """sum_i w_i of a float32 CUDA weight vector in FP64 (fixed order); out: one
+    double on the device (a new one by default, or a view into a record)."""
+    torch = _torch()
+    if not isinstance(w, torch.Tensor) or not w.is_cuda or w.dtype != torch.float32 or not w.is_contiguous():
+        raise TypeError("w must be a contiguous float32 CUDA tensor")
+    if out is None:
+        out = _held_by(torch.empty(1, dtype=torch.float64, device=w.device), stream)
+    _check_out(out, 1, w.device)
+    rc = load().tcorr_weight_total(w.data_ptr(), w.numel(), out.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, "tcorr_weight_total")
     return out
 
 

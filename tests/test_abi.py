@@ -160,6 +160,24 @@ def test_gk_and_einstein_validation(lib):
     assert lib.einstein_slope(FAKE_X, 10, 1.0, 0, 2, 9, D, None) == 1     # dim < 1
 
 
+def test_shard_combine_validation(lib):
+    comb = lib.tcorr_combine_shards
+    assert comb(None, 10, 2, 11, FAKE_OUT, None) == 1
+    assert comb(FAKE_X, 10, 2, 11, None, None) == 1
+    assert comb(FAKE_X, 0, 2, 11, FAKE_OUT, None) == 1          # n < 1
+    assert comb(FAKE_X, 10, 0, 11, FAKE_OUT, None) == 1         # no rows
+    assert comb(FAKE_X, 10, 2, 10, FAKE_OUT, None) == 1         # no room for the weight
+    assert comb(FAKE_X + 4, 10, 2, 11, FAKE_OUT, None) == 2
+    assert comb(FAKE_X, 10, 2, 11, FAKE_OUT + 4, None) == 2
+    assert comb(FAKE_X, 10, 2, 11, FAKE_X + 8 * 12, None) == 1  # output over the rows
+    tot = lib.tcorr_weight_total
+    assert tot(None, 10, FAKE_OUT, None) == 1
+    assert tot(FAKE_X, 0, FAKE_OUT, None) == 1
+    assert tot(FAKE_X, 10, None, None) == 1
+    assert tot(FAKE_X + 2, 10, FAKE_OUT, None) == 2
+    assert tot(FAKE_X, 10, FAKE_OUT + 4, None) == 2
+
+
 def test_batch_validation(lib):
     inst = (tcorr.TcorrInstance * 2)()
     inst[0] = tcorr.TcorrInstance(0, FAKE_X, 100, 10, 50, 1, FAKE_OUT)
@@ -172,6 +190,40 @@ def test_batch_validation(lib):
     assert need >= lib.tcorr_workspace_size(100, 10, 99, 1, 0)
     assert lib.tcorr_batch(inst, 2, 0, FAKE_WS, need - 1, None) == 4
     assert lib.tcorr_batch(inst, 0, 0, FAKE_WS, need, None) == 1
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(kind=-1), 1), (dict(kind=2), 1), (dict(d_x=None), 1), (dict(d_out=None), 1), (dict(T=0), 1),
+    (dict(N=-1), 1), (dict(stride=0), 1), (dict(tau_max=-1), 1), (dict(tau_max=100), 1),
+    (dict(T=(1 << 40) + 1, tau_max=5), 1), (dict(N=1 << 41), 1), (dict(d_x=FAKE_X + 2), 2),
+    (dict(d_out=FAKE_OUT + 4), 2)])
+def test_batch_rejects_a_corrupted_descriptor(lib, bad, code):
+    """One corrupted entry among valid ones: the whole call is refused on the
+    host, before anything is enqueued (the pointers are never dereferenced)."""
+    good = dict(kind=0, d_x=FAKE_X, T=100, N=10, tau_max=50, stride=1, d_out=FAKE_OUT)
+    inst = (tcorr.TcorrInstance * 3)()
+    inst[0] = tcorr.TcorrInstance(**good)
+    inst[1] = tcorr.TcorrInstance(**dict(good, **bad))
+    inst[2] = tcorr.TcorrInstance(**dict(good, kind=1))
+    for method in (0, 4):
+        assert lib.tcorr_batch(inst, 3, method, FAKE_WS, 1 << 40, None) == code, (bad, method)
+
+
+def test_injected_host_allocation_failure_returns_enomem(lib, monkeypatch):
+    """TCORR_FAULT_INJECT=host_alloc fails the batch plan's host allocation:
+    tcorr_batch returns TCORR_ENOMEM (nothing is enqueued: the pointers here are
+    never dereferenced) and the workspace query returns 0."""
+    inst = (tcorr.TcorrInstance * 2)()
+    inst[0] = tcorr.TcorrInstance(0, FAKE_X, 100, 10, 50, 1, FAKE_OUT)
+    inst[1] = tcorr.TcorrInstance(1, FAKE_X, 300, 4, 99, 2, FAKE_OUT + 0x1000)
+    need = {m: lib.tcorr_batch_workspace_size(inst, 2, m) for m in (0, 4)}
+    assert all(v > 0 for v in need.values())
+    monkeypatch.setenv("TCORR_FAULT_INJECT", "host_alloc")
+    for m in (0, 4):
+        assert lib.tcorr_batch_workspace_size(inst, 2, m) == 0
+        assert lib.tcorr_batch(inst, 2, m, FAKE_WS, need[m], None) == 3    # TCORR_ENOMEM
+    monkeypatch.delenv("TCORR_FAULT_INJECT")
+    assert lib.tcorr_batch_workspace_size(inst, 2, 0) == need[0]
 
 
 def test_binding_refuses_cpu_tensors(lib):

@@ -122,3 +122,58 @@ def test_batch_with_a_big_instance(T):
     for kind, x, tm, s, out in dev:
         f = T.tcorr_msd if kind == 0 else T.tcorr_acf
         assert np.array_equal(out.cpu().numpy(), f(x, tm, s, "fp16x3").cpu().numpy()), x.shape
+
+
+@pytest.fixture(scope="module")
+def full_batch(T):
+    """The batching workload at full size, drawn on the device, with the oracle's
+    values at lags 0, 1, tau_max/3, four lags in tau_max-192 .. tau_max-1 and
+    tau_max for every instance."""
+    if torch.cuda.get_device_properties(0).total_memory < 150e9:
+        pytest.skip("needs a large-memory GPU")
+    shapes = synth.batch_workload_shapes(256)
+    data = []
+    for i, shp in enumerate(shapes):
+        kind, Tn, N, tm, s, _ = shp
+        x = synth.batch_instance_device(i, shp)
+        tail = np.linspace(max(0, tm - 192), tm - 1, 4).astype(np.int64)
+        lags = np.unique(np.concatenate([[0, 1, tm // 3, tm], tail]))
+        xh = x.cpu().numpy()
+        ref = (oracle.msd if kind == 0 else oracle.acf)(xh, stride=s, lags=lags)
+        del xh
+        data.append((kind, x, tm, s, lags, ref))
+    yield data
+    del data
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", ["fp16x3", "plain"])
+def test_full_batching_workload_vs_oracle(T, full_batch, method):
+    """The batching workload at full size: 256 uneven instances (N log-uniform
+    in [64, 16384], T uniform in [500, 20000], tau_max = T/4; even: MSD of a
+    random walk, odd: VACF of OU velocities) in one tcorr_batch call, every
+    instance against the oracle at its sampled lags."""
+    items = [(kind, x, tm, s, torch.full((tm + 1,), np.nan, dtype=torch.float64, device="cuda"))
+             for kind, x, tm, s, _, _ in full_batch]
+    inst = T.make_instances(items)
+    T.tcorr_batch(inst, method)
+    torch.cuda.synchronize()
+    assert T.tcorr_status_poll() == 0
+    worst = 0.0
+    for (kind, x, tm, s, out), (_, _, _, _, lags, ref) in zip(items, full_batch):
+        got = out.cpu().numpy()[lags]
+        what = f"{method} instance kind {kind} T={x.shape[0]} N={x.shape[1]}"
+        if method == "plain":
+            if kind == 0:
+                err = parity.check_plain_msd(got, ref, what=what)
+            else:
+                err = parity.check_acf(got, ref, parity.PLAIN_TOL, what=what)
+        else:
+            if kind == 0:
+                assert got[0] == 0.0, what
+                err = parity.check_tc_msd(got, ref, what=what)
+            else:
+                err = parity.check_acf(got, ref, parity.TC_TOL, what=what)
+        worst = max(worst, err)
+    print(f"{method}: worst error over 256 instances {worst:.2e}")

@@ -80,3 +80,36 @@ def test_batch_of_flux_series(T):
     for kind, x, tm, s, o in items:
         single = T.tcorr_acf(x, tm, s, "fp16x3").cpu().numpy()
         assert np.array_equal(o.cpu().numpy(), single)
+
+
+@pytest.mark.slow
+def test_full_flux_workload_vs_oracle(T):
+    """The Green-Kubo flux workload at full size: one T = 2,000,000 series and a
+    batch of 64 series of T = 200,000, tau_max = 20,000, FP16x3 (polyphase),
+    every series against the oracle at 30 lags (the polyphase block edges
+    383/384/767/768, spread lags and the last ones); the batched running
+    integrals of all 65 series against the oracle's integral of the device
+    correlations."""
+    tm = 20000
+    lags = np.unique(np.concatenate([[0, 1, 2, 383, 384, 767, 768, tm - 1, tm],
+                                     np.linspace(0, tm, 21).astype(np.int64)]))
+    longh = synth.ar1_flux(2000000, 0.999, seed=synth.BASE_SEED + 6)
+    shorth = [synth.ar1_flux(200000, 0.999, seed=synth.BASE_SEED + 1000 + i) for i in range(64)]
+    outs = torch.full((65, tm + 1), np.nan, dtype=torch.float64, device="cuda")
+    T.tcorr_acf(dev(longh), tm, 1, "fp16x3", out=outs[0])
+    xs = [dev(a) for a in shorth]
+    inst = T.make_instances([(1, x, tm, 1, outs[1 + i]) for i, x in enumerate(xs)])
+    T.tcorr_batch(inst, "fp16x3")
+    gk = T.gk_integrate_batch(outs, 1.0, 1.0 / 3.0)
+    torch.cuda.synchronize()
+    assert T.tcorr_status_poll() == 0
+    got = outs.cpu().numpy()
+    g = gk.cpu().numpy()
+    worst = 0.0
+    for j, a in enumerate([longh] + shorth):
+        ref = oracle.acf(a, stride=1, lags=lags)
+        worst = max(worst, parity.check_acf(got[j][lags], ref, parity.TC_TOL, what=f"flux series {j}"))
+        # the device integral is that of the device correlation (to FP64 rounding)
+        want = oracle.gk_integrate(got[j], 1.0, 1.0 / 3.0)
+        assert np.allclose(g[j], want, rtol=1e-12, atol=1e-12 * np.abs(want).max()), j
+    print(f"flux workload: worst error {worst:.2e} of C(0) over 65 series")

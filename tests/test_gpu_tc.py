@@ -101,20 +101,39 @@ def test_deterministic(T):
     assert T.tcorr_status_poll() == 0
 
 
-@pytest.mark.slow
-def test_water_scale_sampled_lags(T):
-    """N=32768 (3-site molecules), T=10000, tau_max=2000, FP16x3: sampled lags vs oracle."""
-    Tn, N, tm = 10000, 32768, 2000
+@pytest.fixture(scope="module")
+def water(T):
+    Tn, N = 10000, 32768
     x = synth.random_walk_positions_device(Tn, N, 0.005, 5.0, seed=synth.BASE_SEED,
                                            sites_per_molecule=3)
     v = synth.ou_velocities_device(Tn, N, 0.05, 1.0, seed=synth.BASE_SEED + 1)
-    m = T.tcorr_msd(x, tm, 1, "fp16x3").cpu().numpy()
-    c = T.tcorr_acf(v, tm, 1, "fp16x3").cpu().numpy()
-    lags = np.array([0, 1, 2, 3, 10, 127, 128, 129, 255, 256, 500, 1000, 1999, 2000])
-    xh, vh = x.cpu().numpy(), v.cpu().numpy()
+    yield x, v, x.cpu().numpy(), v.cpu().numpy()
     del x, v
-    rm = oracle.msd(xh, stride=1, lags=lags)
-    rc = oracle.acf(vh, stride=1, lags=lags)
+    torch.cuda.empty_cache()
+
+
+# 48 evenly spaced lags, the first tile edges, and every lag of the last column
+# tile of the band rows (tau_max - 191 .. tau_max)
+WATER_TM = 2000
+WATER_LAGS = np.unique(np.concatenate([
+    np.linspace(0, WATER_TM, 48).astype(np.int64), [1, 2, 3, 10, 127, 128, 129, 191, 192, 255, 256],
+    np.arange(WATER_TM - 191, WATER_TM + 1)]))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("stride", [1, 3])
+def test_water_scale_sampled_lags(T, water, stride):
+    """N=32768 (3-site molecules), T=10000, tau_max=2000, FP16x3: 48 spread lags
+    and the whole last column tile vs the oracle, origin stride 1 and 3."""
+    x, v, xh, vh = water
+    tm = WATER_TM
+    m = T.tcorr_msd(x, tm, stride, "fp16x3").cpu().numpy()
+    c = T.tcorr_acf(v, tm, stride, "fp16x3").cpu().numpy()
+    lags = WATER_LAGS
+    rm = oracle.msd(xh, stride=stride, lags=lags)
+    rc = oracle.acf(vh, stride=stride, lags=lags)
     assert m[0] == 0.0
-    assert np.max(np.abs(m[lags] - rm)) / rm[-1] <= parity.TC_TOL
-    assert np.max(np.abs(c[lags] - rc)) / abs(rc[0]) <= parity.TC_TOL
+    parity.check_tc_msd(m[lags], rm, what=f"water msd, stride {stride}")
+    parity.check_acf(c[lags], rc, parity.TC_TOL, what=f"water acf, stride {stride}")
+
+

@@ -90,30 +90,47 @@ def _atom_worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     x = synth.random_walk_positions(120, 37, 0.02, 2.0, seed=91)
     a0, a1 = shard.atom_range(37, rank, world)
-    # each rank's share: the oracle stands in for the device library on CPU
+    # each rank's share: the oracle stands in for the device library on CPU; the
+    # records are gathered through gloo (the combine itself runs in the library)
     part = torch.from_numpy(oracle.msd(np.ascontiguousarray(x[:, a0:a1]), 60, 2))
-    whole = shard.combine_atom_shards(part, a1 - a0)
+    rows = shard.gather_shard_records(shard.shard_record(part, n_atoms=a1 - a0))
     dist.destroy_process_group()
-    q.put((rank, whole.numpy()))
+    q.put((rank, rows.numpy()))
 
 
-def test_two_gloo_ranks_combine_atom_shards():
+def _run_two(target):
     import torch.multiprocessing as mp
-    import oracle
-    from paper_1708_08619_gb300 import synth
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_atom_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=target, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
     results = [q.get(timeout=120) for _ in procs]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    want = oracle.msd(synth.random_walk_positions(120, 37, 0.02, 2.0, seed=91), 60, 2)
-    for _, got in results:
-        np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+    return sorted(results, key=lambda r: r[0])
+
+
+def test_two_gloo_ranks_gather_atom_shard_records():
+    """Both ranks receive both records, in rank order, each holding that rank's
+    per-lag averages and its atom count; their count-weighted mean is the
+    oracle's average over all atoms."""
+    import oracle
+    from paper_1708_08619_gb300 import synth
+    results = _run_two(_atom_worker)
+    x = synth.random_walk_positions(120, 37, 0.02, 2.0, seed=91)
+    want = oracle.msd(x, 60, 2)
+    for _, rows in results:
+        assert rows.shape == (2, 62)
+        for r in range(2):
+            a0, a1 = shard.atom_range(37, r, 2)
+            assert rows[r, 61] == a1 - a0
+            assert np.array_equal(rows[r, :61], oracle.msd(np.ascontiguousarray(x[:, a0:a1]), 60, 2))
+        w = rows[:, 61]
+        np.testing.assert_allclose((w[:, None] * rows[:, :61]).sum(axis=0) / w.sum(), want, rtol=1e-12, atol=0)
+    assert np.array_equal(results[0][1], results[1][1])
 
 
 def _weighted_atom_worker(rank, world, port, q):
@@ -126,29 +143,22 @@ def _weighted_atom_worker(rank, world, port, q):
     v = synth.ou_velocities(150, 41, 0.1, 1.0, seed=93)
     w = np.random.default_rng(94).uniform(0.5, 16.0, size=41).astype(np.float32)
     a0, a1 = shard.atom_range(41, rank, world)
-    # a weighted share is combined with its weight sum in place of its atom count
+    # a weighted share carries its weight sum in place of its atom count
     part = torch.from_numpy(oracle.acf_weighted(np.ascontiguousarray(v[:, a0:a1]), w[a0:a1], 70, 1))
-    whole = shard.combine_atom_shards(part, float(w[a0:a1].astype(np.float64).sum()))
+    wsum = torch.tensor([float(w[a0:a1].astype(np.float64).sum())], dtype=torch.float64)
+    rows = shard.gather_shard_records(shard.shard_record(part, weight=wsum))
     dist.destroy_process_group()
-    q.put((rank, whole.numpy()))
+    q.put((rank, rows.numpy()))
 
 
-def test_two_gloo_ranks_combine_weighted_atom_shards():
-    import torch.multiprocessing as mp
+def test_two_gloo_ranks_gather_weighted_atom_shard_records():
     import oracle
     from paper_1708_08619_gb300 import synth
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    port = _free_port()
-    procs = [ctx.Process(target=_weighted_atom_worker, args=(r, 2, port, q)) for r in range(2)]
-    for p in procs:
-        p.start()
-    results = [q.get(timeout=120) for _ in procs]
-    for p in procs:
-        p.join(timeout=60)
-        assert p.exitcode == 0
+    results = _run_two(_weighted_atom_worker)
     v = synth.ou_velocities(150, 41, 0.1, 1.0, seed=93)
     w = np.random.default_rng(94).uniform(0.5, 16.0, size=41).astype(np.float32)
     want = oracle.acf_weighted(v, w, 70, 1)
-    for _, got in results:
-        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+    for _, rows in results:
+        wr = rows[:, 71]
+        np.testing.assert_allclose((wr[:, None] * rows[:, :71]).sum(axis=0) / wr.sum(), want, rtol=1e-12,
+                                   atol=1e-15)
