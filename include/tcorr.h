@@ -69,7 +69,10 @@ typedef enum {
     TCORR_EWORKSPACE = 4,    /* ws_bytes smaller than tcorr_workspace_size()    */
     TCORR_ECUDA = 5,         /* a CUDA runtime/driver call or launch failed     */
     TCORR_ETIMEOUT = 6,      /* a device-side bounded wait gave up (status word)*/
-    TCORR_EUNSUPPORTED = 7   /* method cannot run this shape or on this device  */
+    TCORR_EUNSUPPORTED = 7,  /* method cannot run this shape or on this device  */
+    TCORR_EBOUNDS = 8        /* debug build only: a kernel's index check found an
+                                index outside its buffer and skipped the access
+                                (status word)                                   */
 } tcorr_status;
 
 typedef enum {
@@ -90,24 +93,24 @@ typedef enum {
     TCORR_AUTO = 5,          /* the library picks (tensor-core when it can) */
     /* FFT route (not in the paper): per column, the lag sums up to tau_max are
        the inverse transform of the (cross) power spectrum of the column
-       zero-padded to L >= T + tau_max (FP64 transforms by cuFFT, FP64 sums
-       over columns; stride s uses the origin-masked signal on one side).
-       Cost O(K T log T) instead of O(K T tau_max): the choice when tau_max is
-       a large fraction of T.  Plans are created once per shape and device
-       (cuFFT keeps its own small plan data); the work area is the caller's
-       workspace, and tcorr_workspace_size makes CUDA calls for this method
-       (it returns 0 without a device).  Accuracy target: 1e-5 relative to
-       C(0) or MSD(tau_max).  Not available in tcorr_batch or the streamed
-       calls. */
+       zero-padded to L >= T + tau_max (L = 2^a, 3 2^a or 5 2^a), two real
+       columns per complex transform, computed by the library's own
+       transforms in double-float arithmetic (about 48 significant bits),
+       FP64 sums over columns; stride s uses the origin-masked signal on one
+       side.  Cost O(K T log T) instead of O(K T tau_max): the choice when
+       tau_max is a large fraction of T.  Padded lengths up to 2^23
+       (T + tau_max up to 8,388,608); longer series return
+       TCORR_EUNSUPPORTED (TCORR_AUTO then takes the tensor-core route).
+       Accuracy target: 1e-5 relative to C(0) or MSD(tau_max).  Not
+       available in tcorr_batch or the streamed calls. */
     TCORR_FFT = 6
 } tcorr_method;
 
 /*
  * Bytes of device workspace that tcorr_msd / tcorr_acf need for these
- * arguments and this method.  Returns 0 when the arguments are invalid (the
- * call itself then reports the error).  Host arithmetic only, except for the
- * FFT route (TCORR_FFT, or TCORR_AUTO when it picks that route), whose size
- * comes from a cuFFT plan made on the current device.
+ * arguments and this method.  Returns 0 when the arguments are invalid or
+ * the method cannot run this shape (the call itself then reports the error).
+ * Host arithmetic only.
  */
 size_t tcorr_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t stride,
                             int method);
@@ -355,7 +358,9 @@ int tcorr_plain_static(int kind, const float *d_x, int64_t T, int64_t N, int64_t
 /*
  * Synchronises `stream`, then returns and clears the current device's status
  * word: TCORR_OK, or TCORR_ETIMEOUT if a kernel's bounded wait gave up since
- * the last poll, or TCORR_ECUDA if the synchronisation failed.
+ * the last poll, TCORR_EBOUNDS if an index check of a debug build
+ * (libtcorr_debug.so, compiled with TCORR_DEBUG_BOUNDS) failed, or
+ * TCORR_ECUDA if the synchronisation failed.
  */
 int tcorr_status_poll(void *stream);
 

@@ -2,9 +2,8 @@
 
 Each translation unit under csrc/ is compiled in parallel to an object in
 ``_build/``, then linked into ``paper_1708_08619_gb300/libtcorr.so``.  The
-library links the CUDA runtime and cuFFT (the transforms of the FFT route);
-the driver entry point it needs (tensor-map encoding) is looked up at run
-time.
+library links only the CUDA runtime; the driver entry point it needs
+(tensor-map encoding) is looked up at run time.
 """
 from __future__ import annotations
 
@@ -32,8 +31,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+DEBUG_LIB = os.path.join(PKG, "libtcorr_debug.so")
+
+
+def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(
             os.path.getmtime(p) for p in [src] + glob.glob(os.path.join(CSRC, "*.cuh"))
             + glob.glob(os.path.join(ROOT, "include", "*.h"))):
@@ -45,20 +47,26 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
+    """Build libtcorr.so (or, with debug=True, libtcorr_debug.so: the same
+    sources with TCORR_DEBUG_BOUNDS, whose kernels check their global-memory
+    indices and report a bad one as TCORR_EBOUNDS instead of faulting)."""
+    build_dir = os.path.join(BUILD, "debug") if debug else BUILD
+    lib = DEBUG_LIB if debug else LIB
+    flags = (extra or []) + (["-DTCORR_DEBUG_BOUNDS"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra or []), srcs))
+        objs = list(ex.map(lambda s: _compile(s, flags, build_dir), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart", "-lcufft"]
+    if not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", lib] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":

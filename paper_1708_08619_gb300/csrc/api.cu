@@ -92,6 +92,7 @@ int resolve_method(int method, int64_t T, int64_t N, int64_t tau_max, int64_t s)
     (void)s;
     if (method != TCORR_AUTO) return method;
     if (!gram_method_available(TCORR_TC_FP16X3)) return TCORR_PLAIN;
+    if (!fft_supported(T, tau_max)) return TCORR_TC_FP16X3;
     const double L = 2.0 * static_cast<double>(T + tau_max);      // padded length, within 2x
     const double band = 6.5e-15 * static_cast<double>(T) * static_cast<double>(tau_max + 128);
     const double fft = 1.5e-11 * L * std::log2(L);
@@ -509,6 +510,7 @@ const char *tcorr_strerror(int code) {
         case TCORR_ECUDA: return "TCORR_ECUDA: CUDA call failed";
         case TCORR_ETIMEOUT: return "TCORR_ETIMEOUT: device-side wait gave up";
         case TCORR_EUNSUPPORTED: return "TCORR_EUNSUPPORTED: method cannot run this shape";
+        case TCORR_EBOUNDS: return "TCORR_EBOUNDS: index check of a debug build failed";
         default: return "unknown tcorr status";
     }
 }

@@ -137,6 +137,8 @@ struct GramArgs {
     unsigned long long *counter;   // work-item counter (zeroed before the launch)
     int mode;               // 0 = band tiles, 1 = polyphase blocks
     int64_t nq;             // polyphase: block shifts q = 0 .. nq-1
+    int64_t partial_elems;  // doubles in partial (debug builds check the window stores)
+    unsigned int *dbg_status;
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -658,7 +660,8 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 const Item I0 = decode_item(a, local);
                 if (I0.empty) {
                     double *outp0 = a.partial + I0.canon * WPG;
-                    for (int w = et; w < WPG; w += 32 * NEPI) outp0[w] = 0.0;
+                    for (int w = et; w < WPG; w += 32 * NEPI)
+                        if (TCORR_IN_BOUNDS(I0.canon * WPG + w, a.partial_elems, a.dbg_status)) outp0[w] = 0.0;
                     continue;
                 }
                 kb0 = I0.kb0;
@@ -731,7 +734,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                     sum += lagbuf[e * WPG + w];
                     lagbuf[e * WPG + w] = 0.f;
                 }
-                outp[w] = static_cast<double>(sum);
+                if (TCORR_IN_BOUNDS(I.canon * WPG + w, a.partial_elems, a.dbg_status)) outp[w] = static_cast<double>(sum);
             }
             named_bar_sync(1, 32 * NEPI);
         }
@@ -1795,6 +1798,12 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
     ga.b3d = s > 1 ? 1 : 0;
     ga.sub_kb = L.sub_kb;
     ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
+    ga.partial_elems = dbg_shrink_elems(L.p.n_items * WPG, WPG);
+#ifdef TCORR_DEBUG_BOUNDS
+    ga.dbg_status = status_word_device_ptr();
+#else
+    ga.dbg_status = nullptr;
+#endif
     return ga;
 }
 
@@ -1949,6 +1958,12 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
     ga.mode = 1;
     ga.nq = L.nq;
+    ga.partial_elems = dbg_shrink_elems(L.p.n_items * WPG, WPG);
+#ifdef TCORR_DEBUG_BOUNDS
+    ga.dbg_status = status_word_device_ptr();
+#else
+    ga.dbg_status = nullptr;
+#endif
     P->gram.item_begin = 0;
     PolyReduceArgs &ra = P->red;
     ra.partial = ga.partial;
@@ -2458,6 +2473,18 @@ int selftest_timeout(cudaStream_t st) {
     timeout_probe_kernel<<<1, 32, 0, st>>>(10000000ull);   // 10 ms
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TCORR_OK : cuda_fail(e, "timeout_probe_kernel launch");
+}
+
+unsigned int *status_word_device_ptr() {
+    static unsigned int *ptr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+        ptr[dev] = static_cast<unsigned int *>(p);
+    }
+    return ptr[dev];
 }
 
 int status_poll_and_clear(cudaStream_t st) {

@@ -51,6 +51,9 @@ struct PlainArgs {
     double *partial;        // [n_items][WP] of this instance
     int64_t item_begin;     // batch: first global block of this instance
     int kind;               // batch: 0 = MSD, 1 = ACF
+    int64_t x_elems;        // floats in x and in xb (debug builds check the loads against it)
+    int64_t partial_elems;  // doubles in partial (debug builds check the stores against it)
+    unsigned int *dbg_status;
 };
 
 namespace {
@@ -98,7 +101,7 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
     const int64_t o0 = r * BO;
     const int64_t k0 = o0 + c * BF;
     if (c * BF - BO + 1 > m_max || k0 >= n_rho) {   // no pair of this tile is in the band
-        outp[tid] = 0.0;
+        if (TCORR_IN_BOUNDS(item_in * WP + tid, a.partial_elems, a.dbg_status)) outp[tid] = 0.0;
         return;
     }
 
@@ -128,8 +131,10 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
                 const int64_t kg = kc + kk;
                 const bool ok = kg < se;
                 const uint32_t off = static_cast<uint32_t>(((buf * BK + kk) * LDS + lcol) * 4);
-                cp_async4(sA0 + off, ok && vA ? gA + kg : a.x, ok && vA ? 4 : 0);
-                cp_async4(sB0 + off, ok && vB ? gB + kg : a.x, ok && vB ? 4 : 0);
+                const bool la = ok && vA && TCORR_IN_BOUNDS(oA * a.s * a.K + kg, a.x_elems, a.dbg_status);
+                const bool lb = ok && vB && TCORR_IN_BOUNDS((rho + kB * a.s) * a.K + kg, a.x_elems, a.dbg_status);
+                cp_async4(sA0 + off, la ? gA + kg : a.x, la ? 4 : 0);
+                cp_async4(sB0 + off, lb ? gB + kg : a.x, lb ? 4 : 0);
             }
         };
 
@@ -216,7 +221,7 @@ __device__ __forceinline__ void plain_tile_body(const PlainArgs &a, int64_t item
             dacc += static_cast<double>(((sd[0] + sd[1]) + (sd[2] + sd[3])) + ((sd[4] + sd[5]) + (sd[6] + sd[7])));
         }
     }
-    outp[tid] = dacc;
+    if (TCORR_IN_BOUNDS(item_in * WP + tid, a.partial_elems, a.dbg_status)) outp[tid] = dacc;
 }
 
 template <int KIND>
@@ -291,6 +296,13 @@ PlainArgs plain_args(int kind, const float *d_x, const BandPlan &p, double *part
     a.partial = partial;
     a.item_begin = item_begin;
     a.kind = kind;
+    a.x_elems = p.T * p.K;
+    a.partial_elems = dbg_shrink_elems(p.n_items * WP, WP);
+#ifdef TCORR_DEBUG_BOUNDS
+    a.dbg_status = status_word_device_ptr();
+#else
+    a.dbg_status = nullptr;
+#endif
     return a;
 }
 

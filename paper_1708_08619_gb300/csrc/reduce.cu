@@ -40,7 +40,8 @@ __device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t 
         const int64_t c = c_lo + cc;
         const int64_t item = ((gg * a.n_res + rho) * a.n_rows + rr) * a.n_cols + c;
         const int64_t w = m - c * a.BF + a.BO - 1;
-        sum += a.partial[item * a.WP + w];
+        const int64_t at = item * a.WP + w;
+        if (TCORR_IN_BOUNDS(at, a.partial_elems, a.dbg_status)) sum += a.partial[at];
         cc += dc;
         int64_t carry = dq;
         if (cc >= ncs) {
@@ -291,6 +292,12 @@ LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const Fi
                               double *d_out, int64_t lag_begin) {
     LagReduceDesc a;
     a.partial = partial;
+    a.partial_elems = dbg_shrink_elems(p.n_items * p.WP, p.WP);
+#ifdef TCORR_DEBUG_BOUNDS
+    a.dbg_status = status_word_device_ptr();
+#else
+    a.dbg_status = nullptr;
+#endif
     a.T = p.T;
     a.N = p.N;
     a.s = p.s;

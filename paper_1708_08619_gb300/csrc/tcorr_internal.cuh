@@ -90,8 +90,10 @@ int plain_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max,
               const float *d_y = nullptr);
 size_t plain_window_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s, int64_t orig_cap);
 bool corr_sizes_valid(int64_t T, int64_t N, int64_t tau_max, int64_t s);
-// FFT route (fft.cu); its sizes come from cuFFT plans, so it needs a device.
+// FFT route (fft.cu): the library's own double-float transforms; sizes are host arithmetic.
 size_t fft_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int kind);
+// Whether the FFT route handles this padded length (T + tau_max up to about 8.4 million).
+bool fft_supported(int64_t T, int64_t tau_max);
 int fft_run(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, double *d_out,
             void *d_ws, size_t ws_bytes, cudaStream_t st, const float *d_y = nullptr);
 // prefix[rho][j] = sum_{j' < j} S(rho + j' s) for the residues rho < n_res (gram_tc.cu).
@@ -137,6 +139,34 @@ inline void host_alloc_fault_point() {
     if (f && std::string(f) == "host_alloc") throw std::bad_alloc();
 }
 
+// Debug builds (TCORR_DEBUG_BOUNDS, libtcorr_debug.so): kernels check the
+// global-memory indices of the plain path (trajectory loads, partial-sum
+// stores), of the lag reduction (partial-sum loads) and of the band kernel's
+// window stores against the extents of their buffers before the access.  An
+// index outside records TCORR_EBOUNDS in the device status word (read and
+// cleared by tcorr_status_poll) and the access is skipped (a load reads 0), so
+// a bad index shows as an error code instead of a fault.  In release builds
+// the checks compile to nothing.  For a test of the mechanism,
+// TCORR_DEBUG_SHRINK=1 in the environment makes the host declare every
+// partial-sum buffer one window shorter than it is (the real buffer is intact,
+// so the skipped accesses stay harmless) and the checks must fire.
+unsigned int *status_word_device_ptr();     // the status word's device address (gram_tc.cu)
+#ifdef TCORR_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_in_bounds(int64_t i, int64_t n, unsigned int *status) {
+    if (i >= 0 && i < n) return true;
+    atomicExch(status, static_cast<unsigned int>(TCORR_EBOUNDS));
+    return false;
+}
+#define TCORR_IN_BOUNDS(i, n, status) ::tcorr::dbg_in_bounds((i), (n), (status))
+inline int64_t dbg_shrink_elems(int64_t elems, int64_t window) {
+    const char *v = std::getenv("TCORR_DEBUG_SHRINK");
+    return (v && v[0] == '1' && elems >= window) ? elems - window : elems;
+}
+#else
+#define TCORR_IN_BOUNDS(i, n, status) true
+inline int64_t dbg_shrink_elems(int64_t elems, int64_t) { return elems; }
+#endif
+
 // Workspace layout helpers (byte offsets, 256-byte aligned).
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -179,6 +209,8 @@ cudaError_t launch_normalize(double *d_out, int64_t T, int64_t N, int64_t tau_ma
 // One instance of the lag reduction (also one entry of a batch).
 struct LagReduceDesc {
     const double *partial;
+    int64_t partial_elems;    // doubles in partial (debug builds check the loads against it)
+    unsigned int *dbg_status; // the status word (debug builds)
     int64_t T, N, s, tau_max;
     int64_t n_res, n_rows, n_cols, n_groups;
     int BO, BF, WP, mode;

@@ -16,7 +16,8 @@ PLAIN, TC_TF32X3, TC_BF16X3, TC_BF16X4, TC_FP16X3, AUTO, FFT = range(7)
 METHODS = {"plain": PLAIN, "tf32x3": TC_TF32X3, "bf16x3": TC_BF16X3, "bf16x4": TC_BF16X4,
            "fp16x3": TC_FP16X3, "auto": AUTO, "fft": FFT}
 STATUS = {0: "TCORR_OK", 1: "TCORR_EINVAL", 2: "TCORR_EALIGN", 3: "TCORR_ENOMEM",
-          4: "TCORR_EWORKSPACE", 5: "TCORR_ECUDA", 6: "TCORR_ETIMEOUT", 7: "TCORR_EUNSUPPORTED"}
+          4: "TCORR_EWORKSPACE", 5: "TCORR_ECUDA", 6: "TCORR_ETIMEOUT", 7: "TCORR_EUNSUPPORTED",
+          8: "TCORR_EBOUNDS"}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtcorr.so")
 _lib = None

@@ -70,7 +70,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_version_and_strerror(lib):
     assert lib.tcorr_version() >= 100
-    for code in range(8):
+    for code in range(9):
         assert lib.tcorr_strerror(code).startswith(b"TCORR_")
 
 
@@ -305,7 +305,13 @@ def test_xcf_misaligned_and_workspace(lib):
     assert call_xcf(lib, ws_bytes=need - 1) == 4
 
 
-def test_fft_method_is_known():
-    """Method 6 (FFT route) passes argument validation; its workspace size
-    comes from cuFFT plans and is 0 without a device."""
+def test_fft_method_is_known(lib):
+    """Method 6 (FFT route) passes argument validation; its workspace size is
+    host arithmetic (the route's own transforms, no plan on a device), and a
+    padded length beyond the route's 2^23 gives 0."""
     assert tcorr.METHODS["fft"] == 6
+    need = lib.tcorr_workspace_size(1000, 64, 999, 1, 6)
+    assert need >= 32 * 2048 * 16                   # 32 complex rows of the padded length
+    assert lib.tcorr_workspace_size(5000000, 1, 4000000, 1, 6) == 0
+    assert lib.tcorr_workspace_size(4000000, 1, 4000000 - 1, 1, 6) > 0
+    assert call_msd(lib, T=5000000, N=1, tau_max=4000000, method=6) == 7   # TCORR_EUNSUPPORTED

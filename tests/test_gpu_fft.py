@@ -28,6 +28,9 @@ def T():
     (640, 7, 200, 2),
     (300, 1, 299, 1),       # one atom (K = 3)
     (97, 5, 0, 1),          # lag 0 only
+    (12000, 3, 5000, 1),    # L = 5 2^12: column pass of length 8, rows of 2560 (radix-5 stage)
+    (7000, 4, 5000, 2),     # L = 3 2^12: column pass of length 4, rows of 3072 (radix-3), masked
+    (40000, 1, 39999, 1),   # L = 5 2^14: column pass of length 32
 ])
 def test_fft_msd_acf_match_oracle(T, Tn, N, tm, s):
     x = synth.random_walk_positions(Tn, N, 0.01, 3.0, seed=synth.BASE_SEED + Tn + N)
@@ -56,8 +59,8 @@ def test_fft_xcf_matches_oracle(T, s):
 
 
 def test_fft_many_column_chunks(T):
-    """K larger than one chunk of columns (chunks of 2^27 / L columns)."""
-    Tn, N, tm = 4000, 6000, 3999            # L = 8192 -> 16384 columns per chunk, K = 18000
+    """K larger than one chunk of columns (2 x 2^23 / L columns per chunk)."""
+    Tn, N, tm = 4000, 6000, 3999            # L = 8192 -> 2048 columns per chunk, K = 18000: 9 chunks
     v = synth.ou_velocities(Tn, N, 0.1, 1.0, seed=53)
     c = T.tcorr_acf(torch.from_numpy(v).cuda(), tm, 1, "fft").cpu().numpy()
     lags = np.array([0, 1, 2, 100, 1000, 3000, 3999])
@@ -71,3 +74,24 @@ def test_fft_not_in_batch(T):
     inst = T.make_instances([(1, x, 50, 1, out)])
     with pytest.raises(T.TcorrError):
         T.tcorr_batch(inst, "fft")
+
+
+@pytest.mark.slow
+def test_fft_long_series_last_lags(T):
+    """T = 100000 frames with tau_max = T - 1 (padded length 2^18: 64 x 4096).
+    The last lags have n_o = 1, 2, ... origins, so the transform's rounding
+    error, spread evenly over all lags, is divided by a single origin there;
+    the double-float transforms keep it far below 1e-5 of C(0)."""
+    Tn, N = 100000, 2
+    v = synth.ou_velocities(Tn, N, 0.01, 1.0, seed=71)
+    x = synth.random_walk_positions(Tn, N, 0.01, 3.0, seed=72)
+    lags = np.unique(np.concatenate([np.linspace(0, Tn - 1, 40).astype(np.int64), np.arange(Tn - 20, Tn)]))
+    c = T.tcorr_acf(torch.from_numpy(v).cuda(), Tn - 1, 1, "fft").cpu().numpy()
+    m = T.tcorr_msd(torch.from_numpy(x).cuda(), Tn - 1, 1, "fft").cpu().numpy()
+    rc = oracle.acf(v, stride=1, lags=lags)
+    rm = oracle.msd(x, stride=1, lags=lags)
+    err_c = np.max(np.abs(c[lags] - rc)) / abs(rc[0])
+    err_m = np.max(np.abs(m[lags] - rm)) / rm[-1]
+    print(f"fft T={Tn}, tau_max=T-1: acf err {err_c:.2e} of C(0), msd err {err_m:.2e} of MSD(tau_max)")
+    assert err_c <= parity.TC_TOL and err_m <= parity.TC_TOL
+    assert T.tcorr_status_poll() == 0
