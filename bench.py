@@ -170,28 +170,11 @@ def gpu_identifier(torch, dev):
 # built now, per workload.  A capture too large for ncu is taken on the 1/8- or 1/16-atom case
 # of the same T and tau_max and scaled by the atom ratio: operand bytes, tiles and updates all
 # scale with N there.  A workload or method without an entry reports null.
-GRAM_TRAFFIC_BYTES = {("water", "fp16x3"): 8 * (982.221568e6 + 5.485568e6)}
+GRAM_TRAFFIC_BYTES = {("water", "fp16x3"): 8 * (1183.217408e6 + 5.232384e6),
+                      ("precision", "fp16x3"): 16 * (18765.845248e6 + 60.309248e6)}
 # DRAM bytes of one collective_kernel launch on the water-scale velocities (no reference frame):
 # ncu's dram__bytes.sum.per_second x gpu__time_duration.sum.
 COLLECTIVE_WATER_TRAFFIC_BYTES = 6.622334e12 * 594.496e-6
-
-
-def pinned_host(shape):
-    """A float32 host array of exactly this shape in page-locked memory: numpy
-    allocates it and cudaHostRegister pins it (torch's pinned allocator rounds
-    large requests up and its 24 GB buffers copied at about 45 GB/s on the
-    GB300 machine, against 205-211 GB/s for registered memory)."""
-    import torch
-    a = np.empty(shape, dtype=np.float32)
-    a.reshape(-1)[::1024] = 0.0                    # touch the pages from this process first
-    rc = torch.cuda.cudart().cudaHostRegister(a.ctypes.data, a.nbytes, 0)
-    if int(rc) != 0:
-        raise RuntimeError(f"cudaHostRegister failed: {rc}")
-    _REGISTERED.append(a)
-    return torch.from_numpy(a)
-
-
-_REGISTERED = []
 
 
 def peaks():
@@ -453,8 +436,8 @@ def run_gpu(args, wl):
         m_plain = c_plain = None
 
     # ---- host copies (pinned) of the inputs: the oracle reads them, the end-to-end steps upload them
-    xh = pinned_host((T, N, 3))
-    vh = pinned_host((T, N, 3))
+    xh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
+    vh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
     xh.copy_(x)
     vh.copy_(v)
 

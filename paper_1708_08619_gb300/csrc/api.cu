@@ -84,9 +84,10 @@ size_t plain_workspace(int64_t T, int64_t N, int64_t tau_max, int64_t s) {
 // AUTO: the FFT route when its cost estimate is below the band form's, else
 // the FP16 x3 tensor-core form (plain without a tensor-core device).  Costs
 // per K column, calibrated on GB300: band about 6.5e-15 s per (origin, lag)
-// pair (T (tau_max + 128) of them), FFT about 1.5e-11 s per L log2 L of the
-// padded transform length; e.g. T = 2e6 switches to the FFT above
-// tau_max ~ 1.3e5, and T <= 1e5 never does.
+// pair (T (tau_max + 128) of them), FFT about 4e-12 s per L log2 L of the
+// padded transform length (the library's double-float transforms, two
+// columns per complex transform); e.g. T = 2e6 switches to the FFT above
+// tau_max ~ 3e4, T = 1e5 above tau_max ~ 2.3e4.
 int resolve_method(int method, int64_t T, int64_t N, int64_t tau_max, int64_t s) {
     (void)N;
     (void)s;
@@ -95,7 +96,7 @@ int resolve_method(int method, int64_t T, int64_t N, int64_t tau_max, int64_t s)
     if (!fft_supported(T, tau_max)) return TCORR_TC_FP16X3;
     const double L = 2.0 * static_cast<double>(T + tau_max);      // padded length, within 2x
     const double band = 6.5e-15 * static_cast<double>(T) * static_cast<double>(tau_max + 128);
-    const double fft = 1.5e-11 * L * std::log2(L);
+    const double fft = 4e-12 * L * std::log2(L);
     return fft < band ? TCORR_FFT : TCORR_TC_FP16X3;
 }
 
@@ -245,7 +246,7 @@ std::vector<GraphEntry> g_graphs;
 
 std::string knob_string() {
     std::string k;
-    for (const char *name : {"TCORR_KSEG", "TCORR_SUB_KB"}) {
+    for (const char *name : {"TCORR_KSEG", "TCORR_SUB_KB", "TCORR_SUPER"}) {
         const char *v = std::getenv(name);
         k += v ? v : "-";
         k += ';';

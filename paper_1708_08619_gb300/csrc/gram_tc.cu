@@ -113,6 +113,18 @@ int env_sub_kb() {
     return (v >= 1 && v <= 16) ? v : 0;
 }
 
+// TCORR_SUPER=RxC overrides the supertile of the band items' claim order
+// (R row tiles x C column tiles, each 1..4096).
+void supertile_env(int64_t *rows, int64_t *cols) {
+    if (const char *e = std::getenv("TCORR_SUPER")) {
+        long long r = 0, c = 0;
+        if (std::sscanf(e, "%lldx%lld", &r, &c) == 2 && r >= 1 && c >= 1 && r <= 4096 && c <= 4096) {
+            *rows = r;
+            *cols = c;
+        }
+    }
+}
+
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 constexpr size_t SMEM_STAGES = size_t(STAGES) * STAGE_BYTES;
@@ -139,6 +151,7 @@ struct GramArgs {
     int64_t nq;             // polyphase: block shifts q = 0 .. nq-1
     int64_t partial_elems;  // doubles in partial (debug builds check the window stores)
     unsigned int *dbg_status;
+    int64_t super_rows, super_cols;   // band: supertile of the claim order (row tiles x column tiles)
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -324,19 +337,17 @@ __device__ __forceinline__ int item_ncol(int64_t moff, int64_t m_max) {
 }
 
 // Band items are claimed in supertile order: within one (K-group, residue),
-// row tiles are taken kSuperRows at a time and, inside such a row block,
-// column tiles kSuperCols at a time (column fastest).  The ~152 items in
-// flight then form a compact block of the origin x frame plane whose CTAs
-// read the same A rows (one row tile, several columns) and overlapping B rows
-// (neighbouring row tiles are 128 frames apart) at about the same K-block, so
-// the operands are shared in L2.  With column-fastest order over whole rows a
-// band of 53 column tiles (tau_max = 10000) left only about 3 row tiles in
-// flight and each B tile was read from DRAM once per row tile.  The item's
-// partial window is stored at its canonical index
-// ((g n_res + rho) n_rows + r) n_cols + c, which the lag reduction reads.
-constexpr int64_t kSuperRows = 16;
-constexpr int64_t kSuperCols = 10;
-
+// row tiles are taken super_rows at a time and, inside such a row block,
+// column tiles super_cols at a time (column fastest); 16 x 10 by default, the
+// autotuner may pick another shape.  The ~152 items in flight then form a
+// compact block of the origin x frame plane whose CTAs read the same A rows
+// (one row tile, several columns) and overlapping B rows (neighbouring row
+// tiles are 128 frames apart) at about the same K-block, so the operands are
+// shared in L2.  With column-fastest order over whole rows a band of 53
+// column tiles (tau_max = 10000) left only about 3 row tiles in flight and
+// each B tile was read from DRAM once per row tile.  The item's partial
+// window is stored at its canonical index ((g n_res + rho) n_rows + r) n_cols
+// + c, which the lag reduction reads.
 __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
     Item I;
     int64_t t = item;
@@ -344,14 +355,15 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
         const int64_t per = a.n_rows * a.n_cols;
         const int64_t gr = t / per;                          // (K-group, residue) block
         int64_t u = t - gr * per;
-        const int64_t cs = a.n_cols < kSuperCols ? a.n_cols : kSuperCols;
-        const int64_t rb = u / (kSuperRows * a.n_cols);      // row block (all but the last are full)
-        u -= rb * kSuperRows * a.n_cols;
-        const int64_t rcount = min(kSuperRows, a.n_rows - rb * kSuperRows);
+        const int64_t srows = a.super_rows;
+        const int64_t cs = a.n_cols < a.super_cols ? a.n_cols : a.super_cols;
+        const int64_t rb = u / (srows * a.n_cols);           // row block (all but the last are full)
+        u -= rb * srows * a.n_cols;
+        const int64_t rcount = min(srows, a.n_rows - rb * srows);
         const int64_t cb = u / (rcount * cs);                // column block within the row block
         u -= cb * rcount * cs;
         const int64_t ccount = min(cs, a.n_cols - cb * cs);
-        const int64_t r = rb * kSuperRows + u / ccount;
+        const int64_t r = rb * srows + u / ccount;
         const int64_t c = cb * cs + u % ccount;
         I.canon = (gr * a.n_rows + r) * a.n_cols + c;
         I.rho = gr % a.n_res;
@@ -1443,6 +1455,7 @@ struct GramLayout {
     bool x4;
     int64_t Kp, T_pad, n_k, esize, bke, pstride, kseg;
     int sub_kb;
+    int super_rows = kDefaultSuperRows, super_cols = kDefaultSuperCols;   // band claim order
     bool poly;                      // polyphase layout (small K, stride 1)
     int64_t P, Pp, nq, Kprime, Kalloc;
     size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, off_counter, total;
@@ -1479,7 +1492,7 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
     if (L->Kalloc >= (int64_t(1) << 31)) return false;
     const int64_t kb_total = ceil_div(L->Kprime, L->bke);
     {
-        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq), 0};
+        TuneChoice c{tune_default_kseg(L->Kprime, 6 * L->nq, 2), 0};
         if (const TuneChoice *o = get_tune_override()) c = *o;
         if (const int64_t ek = env_kseg()) c.kseg = ek;
         if (c.sub_kb <= 0) c.sub_kb = default_sub_kb(kind, true);
@@ -1547,7 +1560,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     {
         const BandPlan p0 = make_band_plan(T, N, tau_max, s, BO, BF, 64, 1);
         const int64_t tiles = p0.n_res * p0.n_rows * p0.n_cols;
-        TuneChoice c{tune_default_kseg(K, tiles), 0};
+        TuneChoice c{tune_default_kseg(K, tiles, p0.n_cols), 0};
         TuneChoice cached;
         if (const TuneChoice *o = get_tune_override()) c = *o;
         else if (tune_mode() != 0 && tune_lookup(tune_key(method, kind, K, tau_max, T, s), &cached)) c = cached;
@@ -1556,6 +1569,10 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
         if (const int es = env_sub_kb()) c.sub_kb = es;
         L->kseg = c.kseg;
         L->sub_kb = c.sub_kb;
+        if (c.super_rows > 0 && c.super_cols > 0) {
+            L->super_rows = c.super_rows;
+            L->super_cols = c.super_cols;
+        }
     }
     L->p = make_band_plan(T, N, tau_max, s, BO, BF, L->kseg, 1);
     if (w) cap_origins(&L->p, w->orig_cap);
@@ -1804,6 +1821,9 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
 #else
     ga.dbg_status = nullptr;
 #endif
+    ga.super_rows = L.super_rows;
+    ga.super_cols = L.super_cols;
+    supertile_env(&ga.super_rows, &ga.super_cols);
     return ga;
 }
 
@@ -1958,6 +1978,8 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
     ga.mode = 1;
     ga.nq = L.nq;
+    ga.super_rows = kDefaultSuperRows;
+    ga.super_cols = kDefaultSuperCols;
     ga.partial_elems = dbg_shrink_elems(L.p.n_items * WPG, WPG);
 #ifdef TCORR_DEBUG_BOUNDS
     ga.dbg_status = status_word_device_ptr();

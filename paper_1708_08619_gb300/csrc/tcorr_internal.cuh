@@ -108,12 +108,18 @@ inline int cuda_fail(cudaError_t e, const char *what) {
 }
 
 // Autotuner (tune.cu): per shape bucket, the tensor-core work-item length
-// (kseg, K elements) and accumulation sub-chain length (sub_kb, K-blocks;
-// 0 = the default for the kind and form).
+// (kseg, K elements), the accumulation sub-chain length (sub_kb, K-blocks;
+// 0 = the default for the kind and form) and the supertile of the band items'
+// claim order (super_rows x super_cols tiles; 0 = the default).
 struct TuneChoice {
     int64_t kseg;
     int sub_kb;
+    int super_rows = 0;
+    int super_cols = 0;
 };
+// The default supertile (claim order) of the band kernel: 16 x 10 tiles.
+constexpr int kDefaultSuperRows = 16;
+constexpr int kDefaultSuperCols = 10;
 int tune_mode();   // 0 off, 1 tune once per bucket, 2 re-tune every call
 std::string tune_key(int method, int kind, int64_t K, int64_t tau_max, int64_t T, int64_t s);
 bool tune_lookup(const std::string &key, TuneChoice *c);
@@ -122,7 +128,7 @@ const std::vector<TuneChoice> &tune_candidates();
 int64_t tune_min_kseg();
 void set_tune_override(const TuneChoice *c);
 const TuneChoice *get_tune_override();
-int64_t tune_default_kseg(int64_t K, int64_t tiles);
+int64_t tune_default_kseg(int64_t K, int64_t tiles, int64_t n_cols);
 
 // Diagnostics (profile.cu): events around one launch of the dominant kernel.
 // kind: 0 MSD, 1 ACF, 2 a batched launch mixing both.

@@ -31,10 +31,62 @@ def test_tuner_times_candidates_once_and_persists(T, tmp_path, monkeypatch):
     m1 = T.tcorr_msd(xd, 500, 1, "fp16x3").cpu().numpy()
     lines = [json.loads(l) for l in cache.read_text().splitlines() if l.strip()]
     assert len(lines) == 1 and lines[0]["key"].startswith("m4.k0.")
-    # only the work-item length is tuned; sub_kb 0 keeps the accuracy-chosen default
+    # the work-item length and the supertile of the claim order are tuned; sub_kb 0 keeps
+    # the accuracy-chosen default
     assert lines[0]["kseg"] in (4096, 8192, 16384) and lines[0]["sub_kb"] == 0
+    assert (lines[0]["super_rows"], lines[0]["super_cols"]) in ((16, 10), (32, 5), (8, 19))
     m2 = T.tcorr_msd(xd, 500, 1, "fp16x3").cpu().numpy()
     assert np.array_equal(m1, m2)                    # same tuned choice, no second tuning
     assert len(cache.read_text().splitlines()) == 1
     parity.check_tc_msd(m1, oracle.msd(x, 500, 1), what="tuned fp16x3 msd")
     assert T.tcorr_status_poll() == 0
+
+
+def test_every_supertile_shape_gives_the_same_sums(T, monkeypatch):
+    """The claim order only changes which CTA runs an item: the windows land at
+    their canonical index and the lag reduction sums them in a fixed order, so
+    the results are bit-identical for every supertile shape (edge cases: one
+    tile at a time, whole rows, shapes that do not divide the grid)."""
+    x = torch.from_numpy(synth.random_walk_positions(3000, 400, 0.01, 3.0, seed=33)).cuda()
+    ref = {}
+    for shape in ("16x10", "1x1", "1x4096", "4096x1", "7x3", "32x5"):
+        monkeypatch.setenv("TCORR_SUPER", shape)
+        for s in (1, 3):
+            m = T.tcorr_msd(x, 1500, s, "fp16x3").cpu().numpy()
+            ref.setdefault(s, m)
+            assert np.array_equal(m, ref[s]), (shape, s)
+    assert T.tcorr_status_poll() == 0
+
+
+_CHILD = """
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1708_08619_gb300 import build, synth, tcorr
+build.build(); tcorr.load()
+x = torch.from_numpy(synth.random_walk_positions(1200, 300, 0.01, 3.0, seed=34)).cuda()
+m = tcorr.tcorr_msd(x, 400, 1, "fp16x3").cpu().numpy()
+print(float(m[-1]))
+"""
+
+
+def test_cache_lines_without_a_supertile_are_read(T, tmp_path):
+    """A cache line written before the supertile was tuned (kseg and sub_kb only)
+    is read at the first lookup of a fresh process and used: no tuning run
+    follows, so nothing is appended to the file."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = _CHILD.format(root=root)
+    new = tmp_path / "new.jsonl"
+    env = dict(os.environ, TCORR_TUNE="1", TCORR_TUNE_CACHE=str(new))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    key = json.loads(new.read_text().splitlines()[0])["key"]
+    old = tmp_path / "old.jsonl"
+    old.write_text(json.dumps({"key": key, "kseg": 4096, "sub_kb": 0}) + "\n")
+    env["TCORR_TUNE_CACHE"] = str(old)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert len(old.read_text().splitlines()) == 1          # the old line was used, no re-tuning
+    assert np.isfinite(float(r.stdout.strip().splitlines()[-1]))
