@@ -52,6 +52,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "tcorr_internal.cuh"
@@ -125,6 +126,7 @@ void supertile_env(int64_t *rows, int64_t *cols) {
     }
 }
 
+
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 constexpr size_t SMEM_STAGES = size_t(STAGES) * STAGE_BYTES;
@@ -144,7 +146,7 @@ struct GramArgs {
     int64_t scale_stride;   // band: T_pad (one row of scales per K-group); polyphase: 0
     const float *inv_scale_b;   // scales of the frame (column) operand: B's for a cross-correlation
     double *partial;        // [n_items][WPG]
-    int b3d;                // B map is 3-D (K, residue, frame index) when s > 1
+    int b3d;                // 0 band, stride 1; 1 band, stride > 1; 2 polyphase (tensor maps)
     int sub_kb;             // K-blocks per accumulation sub-chain
     unsigned long long *counter;   // work-item counter (zeroed before the launch)
     int mode;               // 0 = band tiles, 1 = polyphase blocks
@@ -152,6 +154,9 @@ struct GramArgs {
     int64_t partial_elems;  // doubles in partial (debug builds check the window stores)
     unsigned int *dbg_status;
     int64_t super_rows, super_cols;   // band: supertile of the claim order (row tiles x column tiles)
+    const uint8_t *xa_h, *xa_l;       // band: tile images of the origin (A) operand, hi / lo
+    const uint8_t *xb_h, *xb_l;       // band: tile images of the frame (B) operand, hi / lo
+    int64_t nkp, rows;                // band: tile-image rows per residue / per K-block plane
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -217,6 +222,12 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
+}
+// Plain bulk copy global -> shared (contiguous bytes, 16-byte aligned).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -540,43 +551,57 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             const GramArgs &a = *resolve(src, item, local, mp);
             const Item I = decode_item(a, local);
             if (I.empty) continue;
-            if (mp[0] != last_map) {      // new instance: bring its descriptors close to the TMA unit
-                for (int i = 0; i < NMAPS; ++i) prefetch_tensormap(mp[i]);
-                last_map = mp[0];
-            }
             const int b3d = a.b3d;
-            const int32_t ay = static_cast<int32_t>(I.a_y), by = static_cast<int32_t>(I.b_y);
-            const int32_t bz = static_cast<int32_t>(I.b_z), bx = static_cast<int32_t>(I.b_x);
-            // a full tile loads B as one BF-row box; a narrow one only the NBOX-row boxes it uses
+            // a full tile loads BF rows of B; a narrow one only the NBOX-row groups it uses
             const bool narrow = I.ncol < BF;
             const int nbox = narrow ? (I.ncol + NBOX - 1) / NBOX : 1;
-            const CUtensorMap *mbh = narrow ? mp[4] : mp[2], *mbl = narrow ? mp[5] : mp[3];
             const int32_t brows = narrow ? NBOX : BF;
-            const uint32_t stage_tx = 2 * A_BYTES + 2 * nbox * brows * ROWB;
-            for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
-                if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
-                mbar_arrive_expect_tx(full_bar(st), stage_tx);
-                const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
-                const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
-                tma_load_2d(sbase, mp[0], kx, ay, full_bar(st));
-                tma_load_2d(sbase + A_BYTES, mp[1], kx, ay, full_bar(st));
-                for (int j = 0; j < nbox; ++j) {
-                    const uint32_t sh = sbase + 2 * A_BYTES + j * NBOX_BYTES, sl = sh + B_BYTES;
-                    const int32_t byj = by + j * NBOX;
-                    if (b3d == 2) {      // polyphase: (K + aligned shift, phase row, shifted copy)
-                        tma_load_3d(sh, mbh, kx + bx, byj, bz, full_bar(st));
-                        tma_load_3d(sl, mbl, kx + bx, byj, bz, full_bar(st));
-                    } else if (b3d) {    // band, stride > 1: (K, residue, frame index)
-                        tma_load_3d(sh, mbh, kx, bz, byj, full_bar(st));
-                        tma_load_3d(sl, mbl, kx, bz, byj, full_bar(st));
-                    } else {
-                        tma_load_2d(sh, mbh, kx, byj, full_bar(st));
-                        tma_load_2d(sl, mbl, kx, byj, full_bar(st));
+            const uint32_t b_bytes = static_cast<uint32_t>(nbox * brows * ROWB);
+            const uint32_t stage_tx = 2 * A_BYTES + 2 * b_bytes;
+            if (b3d == 2) {
+                // polyphase: tensor maps over row-major (K, phase row, shifted copy) operands
+                if (mp[0] != last_map) {      // new instance: bring its descriptors close to the TMA unit
+                    for (int i = 0; i < NMAPS; ++i) prefetch_tensormap(mp[i]);
+                    last_map = mp[0];
+                }
+                const int32_t ay = static_cast<int32_t>(I.a_y), by = static_cast<int32_t>(I.b_y);
+                const int32_t bz = static_cast<int32_t>(I.b_z), bx = static_cast<int32_t>(I.b_x);
+                const CUtensorMap *mbh = narrow ? mp[4] : mp[2], *mbl = narrow ? mp[5] : mp[3];
+                for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
+                    if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
+                    mbar_arrive_expect_tx(full_bar(st), stage_tx);
+                    const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
+                    const int32_t kx = static_cast<int32_t>(kb * (PREC == P_TF32 ? 16 : 32));
+                    tma_load_2d(sbase, mp[0], kx, ay, full_bar(st));
+                    tma_load_2d(sbase + A_BYTES, mp[1], kx, ay, full_bar(st));
+                    for (int j = 0; j < nbox; ++j) {
+                        const uint32_t sh = sbase + 2 * A_BYTES + j * NBOX_BYTES, sl = sh + B_BYTES;
+                        tma_load_3d(sh, mbh, kx + bx, by + j * NBOX, bz, full_bar(st));
+                        tma_load_3d(sl, mbl, kx + bx, by + j * NBOX, bz, full_bar(st));
+                    }
+                    if (++st == STAGES) {
+                        st = 0;
+                        ph ^= 1u;
                     }
                 }
-                if (++st == STAGES) {
-                    st = 0;
-                    ph ^= 1u;
+            } else {
+                // band: each operand tile is one contiguous, pre-swizzled piece of its
+                // K-block plane (A: residue 0, rows o0 ..; B: residue rho, rows k0 ..)
+                const int64_t ra = I.a_y, rb = I.b_z * a.nkp + I.b_y;
+                for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
+                    if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto producer_done;
+                    mbar_arrive_expect_tx(full_bar(st), stage_tx);
+                    const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES);
+                    const int64_t plane = kb * a.rows;
+                    const int64_t oa = (plane + ra) * ROWB, ob = (plane + rb) * ROWB;
+                    bulk_load(sbase, a.xa_h + oa, A_BYTES, full_bar(st));
+                    bulk_load(sbase + A_BYTES, a.xa_l + oa, A_BYTES, full_bar(st));
+                    bulk_load(sbase + 2 * A_BYTES, a.xb_h + ob, b_bytes, full_bar(st));
+                    bulk_load(sbase + 2 * A_BYTES + B_BYTES, a.xb_l + ob, b_bytes, full_bar(st));
+                    if (++st == STAGES) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
         }
@@ -732,7 +757,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             for (int jj = 0; jj < BF / 2; ++jj) {
                 const int j = (BF / 2) * half + jj;
                 const int64_t m = mrow + j;
-                if (m >= 0 && m <= I.m_max) {
+                if (m >= 0 && m <= I.m_max && row < I.a_rows) {
                     float val = acc2[jj];
                     if (PREC == P_FP16) val = (val * rs) * cs[j];
                     atomicAdd(&lb[j - row + (BO - 1)], val);
@@ -794,8 +819,22 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
+// Band operand layout (tile images).  K-block kb (64 bytes of K) of frame
+// t = rho + kk s sits in row R = rho nkp + kk of plane kb; a plane holds
+// rows = s nkp rows, nkp >= n_k + BF per residue, and the rows past n_k are
+// zero.  The rows of one tile (consecutive kk of one residue) are then one
+// contiguous piece of memory, stored as the 64B-swizzled shared-memory image
+// the MMA reads: in row R the 16-byte chunk c sits at position
+// c ^ ((R >> 1) & 3).  Tiles start at rows that are multiples of 8, so one
+// bulk copy of the piece reproduces the image in shared memory.
+__device__ __forceinline__ int64_t tile_chunk_byte(int64_t kb, int64_t R, int64_t rows, int c) {
+    return (kb * rows + R) * 64 + (static_cast<int64_t>(c ^ static_cast<int>((R >> 1) & 3)) << 4);
+}
+
+// Eight values x scaled (FP16) and split into hi / lo, packed as they are
+// stored: two 16-byte vectors each for TF32, one each for FP16 / BF16.
 template <int PREC>
-__device__ __forceinline__ void split_store8(const float (&x)[8], float scale, void *Xh, void *Xl, int64_t off) {
+__device__ __forceinline__ void split_pack8(const float (&x)[8], float scale, uint4 (&vh)[2], uint4 (&vl)[2]) {
     if (PREC == P_TF32) {
         uint32_t h[8], l[8];
 #pragma unroll
@@ -803,12 +842,10 @@ __device__ __forceinline__ void split_store8(const float (&x)[8], float scale, v
             h[i] = tf32_rna(x[i]);
             l[i] = tf32_rna(x[i] - __uint_as_float(h[i]));
         }
-        uint4 *ph = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xh) + off);
-        uint4 *pl = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(Xl) + off);
-        ph[0] = make_uint4(h[0], h[1], h[2], h[3]);
-        ph[1] = make_uint4(h[4], h[5], h[6], h[7]);
-        pl[0] = make_uint4(l[0], l[1], l[2], l[3]);
-        pl[1] = make_uint4(l[4], l[5], l[6], l[7]);
+        vh[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        vh[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        vl[0] = make_uint4(l[0], l[1], l[2], l[3]);
+        vl[1] = make_uint4(l[4], l[5], l[6], l[7]);
     } else {
         uint16_t h[8], l[8];
 #pragma unroll
@@ -826,17 +863,50 @@ __device__ __forceinline__ void split_store8(const float (&x)[8], float scale, v
                 l[i] = __bfloat16_as_ushort(ll);
             }
         }
-        uint4 vh, vl;
-        vh.x = h[0] | (uint32_t(h[1]) << 16);
-        vh.y = h[2] | (uint32_t(h[3]) << 16);
-        vh.z = h[4] | (uint32_t(h[5]) << 16);
-        vh.w = h[6] | (uint32_t(h[7]) << 16);
-        vl.x = l[0] | (uint32_t(l[1]) << 16);
-        vl.y = l[2] | (uint32_t(l[3]) << 16);
-        vl.z = l[4] | (uint32_t(l[5]) << 16);
-        vl.w = l[6] | (uint32_t(l[7]) << 16);
-        *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xh) + off) = vh;
-        *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Xl) + off) = vl;
+        vh[0] = make_uint4(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16),
+                           h[4] | (uint32_t(h[5]) << 16), h[6] | (uint32_t(h[7]) << 16));
+        vl[0] = make_uint4(l[0] | (uint32_t(l[1]) << 16), l[2] | (uint32_t(l[3]) << 16),
+                           l[4] | (uint32_t(l[5]) << 16), l[6] | (uint32_t(l[7]) << 16));
+        vh[1] = vl[1] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+// Band: the eight values of row R at K positions k0 .. k0+7 (k0 a multiple
+// of 8), stored at their tile-image places.
+template <int PREC>
+__device__ __forceinline__ void split_store8(const float (&x)[8], float scale, void *Xh, void *Xl, int64_t R,
+                                             int64_t k0, int64_t rows) {
+    uint8_t *bh = static_cast<uint8_t *>(Xh), *bl = static_cast<uint8_t *>(Xl);
+    uint4 vh[2], vl[2];
+    split_pack8<PREC>(x, scale, vh, vl);
+    if (PREC == P_TF32) {
+        const int64_t kb = k0 / 16;
+        const int c0 = static_cast<int>((k0 % 16) / 4);
+        const int64_t o0 = tile_chunk_byte(kb, R, rows, c0), o1 = tile_chunk_byte(kb, R, rows, c0 + 1);
+        *reinterpret_cast<uint4 *>(bh + o0) = vh[0];
+        *reinterpret_cast<uint4 *>(bh + o1) = vh[1];
+        *reinterpret_cast<uint4 *>(bl + o0) = vl[0];
+        *reinterpret_cast<uint4 *>(bl + o1) = vl[1];
+    } else {
+        const int64_t o = tile_chunk_byte(k0 / 32, R, rows, static_cast<int>((k0 % 32) / 8));
+        *reinterpret_cast<uint4 *>(bh + o) = vh[0];
+        *reinterpret_cast<uint4 *>(bl + o) = vl[0];
+    }
+}
+
+// Polyphase: the eight values at element offset off of a row-major array.
+template <int PREC>
+__device__ __forceinline__ void split_store8_rm(const float (&x)[8], float scale, void *Xh, void *Xl, int64_t off) {
+    uint4 vh[2], vl[2];
+    split_pack8<PREC>(x, scale, vh, vl);
+    constexpr int ES = PREC == P_TF32 ? 4 : 2;
+    uint4 *ph = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(Xh) + off * ES);
+    uint4 *pl = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(Xl) + off * ES);
+    ph[0] = vh[0];
+    pl[0] = vl[0];
+    if (PREC == P_TF32) {
+        ph[1] = vh[1];
+        pl[1] = vl[1];
     }
 }
 
@@ -872,6 +942,7 @@ struct SplitDesc {
     const float *X;
     const float *ref;         // MSD: the reference frame's row (the middle frame)
     int64_t T, K, Kp, T_pad, kseg, n_groups;
+    int64_t s, n_k, nkp, rows;   // tile-image rows: R = (t % s) nkp + t / s, rows = s nkp per plane
     void *Xh, *Xl;
     float *inv_scale;
     double *S;
@@ -914,19 +985,23 @@ __device__ __forceinline__ float fp16_scale(float mx, float *red_f, float *inv_o
 // group's part of S(t) = |x_t|^2 in FP64.  A group of up to 8 x 2048 columns
 // is held in registers: one read from DRAM, then the max, then the stores.
 template <int PREC, int KIND, bool VEC>
-__device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_t g) {
+__device__ __forceinline__ void split_body(const SplitDesc &q, int64_t R, int64_t g) {
     __shared__ float red_f[PREP_THREADS / 32];
     __shared__ double red_d[PREP_THREADS / 32];
+    __shared__ float inv_dummy;
     const int tid = threadIdx.x;
     const float *X = q.X;
-    const bool live = t < q.T;
+    const int64_t rho = R / q.nkp, kk = R - rho * q.nkp;
+    const int64_t t = rho + kk * q.s;
+    const bool real = kk < q.n_k;              // a frame < T_pad (else a zero pad row)
+    const bool live = real && t < q.T;
     const float *row = X + (live ? t : 0) * q.K;
     const int64_t Klive = live ? q.K : 0;      // padding rows are all zero
     const int64_t kb = g * q.kseg;
     const int64_t ke = g == q.n_groups - 1 ? q.Kp : min(q.Kp, kb + q.kseg);
     constexpr int64_t STEP = PREP_THREADS * 8;
     constexpr int NCH = 8;
-    float *inv_out = q.inv_scale + g * q.T_pad + t;
+    float *inv_out = real ? q.inv_scale + g * q.T_pad + t : &inv_dummy;
     float scale = 1.f;
     double sacc = 0.0;
     if (ke - kb <= NCH * STEP) {
@@ -982,7 +1057,7 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
                     for (int i = 0; i < 8; ++i) sq = fmaf(x[c][i], x[c][i], sq);
                     sacc += static_cast<double>(sq);
                 }
-                split_store8<PREC>(x[c], scale, q.Xh, q.Xl, t * q.Kp + k0);
+                split_store8<PREC>(x[c], scale, q.Xh, q.Xl, R, k0, q.rows);
             }
         }
     } else {
@@ -1006,7 +1081,7 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
                 for (int i = 0; i < 8; ++i) sq = fmaf(x[i], x[i], sq);
                 sacc += static_cast<double>(sq);
             }
-            split_store8<PREC>(x, scale, q.Xh, q.Xl, t * q.Kp + k0);
+            split_store8<PREC>(x, scale, q.Xh, q.Xl, R, k0, q.rows);
         }
     }
     if (KIND == 0 && q.S != nullptr) {
@@ -1026,11 +1101,14 @@ __device__ __forceinline__ void split_body(const SplitDesc &q, int64_t t, int64_
 // One warp per (frame t, K-group g) of at most kWarpSeg columns: the same
 // values as split_body, with warp shuffles in place of block reductions.
 template <int PREC, int KIND, bool VEC>
-__device__ __forceinline__ void split_warp_body(const SplitDesc &q, int64_t t, int64_t g) {
-    if (t >= q.T_pad) return;                  // past the last padded frame (whole warp)
+__device__ __forceinline__ void split_warp_body(const SplitDesc &q, int64_t R, int64_t g) {
+    if (R >= q.rows) return;                   // past the last row of the plane (whole warp)
     const int lane = threadIdx.x & 31;
     const float *X = q.X;
-    const bool live = t < q.T;
+    const int64_t rho = R / q.nkp, kk = R - rho * q.nkp;
+    const int64_t t = rho + kk * q.s;
+    const bool real = kk < q.n_k;
+    const bool live = real && t < q.T;
     const float *row = X + (live ? t : 0) * q.K;
     const int64_t Klive = live ? q.K : 0;
     const int64_t kb = g * q.kseg;
@@ -1062,7 +1140,7 @@ __device__ __forceinline__ void split_warp_body(const SplitDesc &q, int64_t t, i
             e = e < -60 ? -60 : (e > 60 ? 60 : e);
         }
         scale = ldexpf(1.f, e);
-        if (lane == 0) q.inv_scale[g * q.T_pad + t] = ldexpf(1.f, -e);
+        if (lane == 0 && real) q.inv_scale[g * q.T_pad + t] = ldexpf(1.f, -e);
     }
     double sacc = 0.0;
 #pragma unroll
@@ -1075,7 +1153,7 @@ __device__ __forceinline__ void split_warp_body(const SplitDesc &q, int64_t t, i
                 for (int i = 0; i < 8; ++i) sq = fmaf(x[c][i], x[c][i], sq);
                 sacc += static_cast<double>(sq);
             }
-            split_store8<PREC>(x[c], scale, q.Xh, q.Xl, t * q.Kp + k0);
+            split_store8<PREC>(x[c], scale, q.Xh, q.Xl, R, k0, q.rows);
         }
     }
     if (KIND == 0 && q.S != nullptr) {
@@ -1349,7 +1427,7 @@ __device__ __forceinline__ void poly_split_body(const PolyPrepArgs &a, int64_t t
 #pragma unroll
         for (int i = 0; i < 8; ++i) x[i] = V[(oct * 8 + r + i) * PT_LD + j];
         const int64_t off = (static_cast<int64_t>(r) * POLY_L + j) * a.Kalloc + k0 + oct * 8;
-        split_store8<PREC>(x, sc[j], a.Yh, a.Yl, off);
+        split_store8_rm<PREC>(x, sc[j], a.Yh, a.Yl, off);
     }
 }
 
@@ -1456,6 +1534,7 @@ struct GramLayout {
     int64_t Kp, T_pad, n_k, esize, bke, pstride, kseg;
     int sub_kb;
     int super_rows = kDefaultSuperRows, super_cols = kDefaultSuperCols;   // band claim order
+    int64_t nkp = 0, rows = 0;      // band tile images: rows per residue (>= n_k + BF) and per plane (s nkp)
     bool poly;                      // polyphase layout (small K, stride 1)
     int64_t P, Pp, nq, Kprime, Kalloc;
     size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, off_counter, total;
@@ -1555,6 +1634,8 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     if (L->poly) return make_poly_layout(T, N, tau_max, method, kind, L);
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
+    L->nkp = ceil_div(L->n_k + BF, 8) * 8;   // a tile starting at a real row never leaves its residue
+    L->rows = s * L->nkp;
     L->T_pad = L->n_k * s;           // rows rho + k s for every rho < s, k < n_k exist
     // kseg / sub_kb: tuning override, then environment, then tuned cache, then defaults
     {
@@ -1585,19 +1666,19 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->p.n_items = L->p.n_groups * L->p.n_res * L->p.n_rows * L->p.n_cols;
     L->pstride = (T - 1) / s + 2;
     // TMA coordinates are 32-bit
-    if (L->Kp >= (int64_t(1) << 31) || L->T_pad >= (int64_t(1) << 31)) return false;
+    if (L->Kp >= (int64_t(1) << 31) || L->rows >= (int64_t(1) << 31)) return false;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off = align256(off + bytes);
         return o;
     };
-    L->off_xh = take(size_t(L->T_pad) * L->Kp * L->esize);
-    L->off_xl = take(size_t(L->T_pad) * L->Kp * L->esize);
+    L->off_xh = take(size_t(L->rows) * L->Kp * L->esize);
+    L->off_xl = take(size_t(L->rows) * L->Kp * L->esize);
     L->off_scale = take(size_t(L->p.n_groups) * L->T_pad * sizeof(float));
     if (L->cross) {
-        L->off_bh = take(size_t(L->T_pad) * L->Kp * L->esize);
-        L->off_bl = take(size_t(L->T_pad) * L->Kp * L->esize);
+        L->off_bh = take(size_t(L->rows) * L->Kp * L->esize);
+        L->off_bl = take(size_t(L->rows) * L->Kp * L->esize);
         L->off_scale_b = take(size_t(L->p.n_groups) * L->T_pad * sizeof(float));
     }
     L->off_S = take(kind == 0 ? size_t(L->p.n_groups) * T * sizeof(double) : 0);
@@ -1670,7 +1751,7 @@ bool split_warp_mode(const GramLayout &L) {
 }
 
 int64_t split_block_count(const GramLayout &L) {
-    return split_warp_mode(L) ? ceil_div(L.T_pad, kWarpFrames) * L.p.n_groups : L.T_pad * L.p.n_groups;
+    return split_warp_mode(L) ? ceil_div(L.rows, kWarpFrames) * L.p.n_groups : L.rows * L.p.n_groups;
 }
 
 // The MSD is unchanged by a constant shift of an atom's positions, so any
@@ -1687,6 +1768,10 @@ SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *bas
     q.T = L.p.T;
     q.K = L.p.K;
     q.Kp = L.Kp;
+    q.s = L.p.s;
+    q.n_k = L.n_k;
+    q.nkp = L.nkp;
+    q.rows = L.rows;
     q.T_pad = L.T_pad;
     q.kseg = (L.kseg / L.bke) * L.bke;     // the K range of one Gram work item
     q.n_groups = L.p.n_groups;
@@ -1703,9 +1788,9 @@ SplitDesc split_desc(int kind, const float *X, const GramLayout &L, uint8_t *bas
 
 template <int PREC>
 cudaError_t launch_split(const SplitDesc &q, cudaStream_t st) {
-    if (q.n_groups > 65535 || q.T_pad > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (q.n_groups > 65535 || q.rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (q.warp_mode) {
-        const dim3 gw(static_cast<unsigned>(ceil_div(q.T_pad, kWarpFrames)), static_cast<unsigned>(q.n_groups));
+        const dim3 gw(static_cast<unsigned>(ceil_div(q.rows, kWarpFrames)), static_cast<unsigned>(q.n_groups));
         if (q.kind == 0) {
             if (q.vec) split_warp_kernel<PREC, 0, true><<<gw, PREP_THREADS, 0, st>>>(q);
             else split_warp_kernel<PREC, 0, false><<<gw, PREP_THREADS, 0, st>>>(q);
@@ -1715,7 +1800,7 @@ cudaError_t launch_split(const SplitDesc &q, cudaStream_t st) {
         }
         return cudaGetLastError();
     }
-    const dim3 g(static_cast<unsigned>(q.T_pad), static_cast<unsigned>(q.n_groups));
+    const dim3 g(static_cast<unsigned>(q.rows), static_cast<unsigned>(q.n_groups));
     if (q.kind == 0) {
         if (q.vec) split_kernel<PREC, 0, true><<<g, PREP_THREADS, 0, st>>>(q);
         else split_kernel<PREC, 0, false><<<g, PREP_THREADS, 0, st>>>(q);
@@ -1749,48 +1834,11 @@ cudaError_t launch_split_batch_class(int cls, const SplitDesc *d, int n, int64_t
 
 // Tensor maps of one instance: A rows are origins o (frame o s); B rows are
 // frames rho + k s (2-D map for s = 1, (K, residue, frame index) for s > 1).
-int encode_maps(const GramLayout &L, uint8_t *base, int64_t s, CUtensorMap *maps) {
-    EncodeFn encode = get_encode();
-    if (!encode) return TCORR_EUNSUPPORTED;
-    const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                   : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    void *bases[2] = {base + L.off_xh, base + L.off_xl};
-    void *bbases[2] = {base + (L.cross ? L.off_bh : L.off_xh), base + (L.cross ? L.off_bl : L.off_xl)};
-    const cuuint64_t rowb = static_cast<cuuint64_t>(L.Kp * L.esize);
-    const cuuint32_t es2[2] = {1, 1};
-    for (int h = 0; h < 2; ++h) {
-        const cuuint64_t dimA[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.p.n_orig)};
-        const cuuint64_t strA[1] = {rowb * static_cast<cuuint64_t>(s)};
-        const cuuint32_t boxA[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(BO)};
-        if (encode(&maps[h], dt, 2, bases[h], dimA, strA, boxA, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (A)");
-        for (int v = 0; v < 2; ++v) {          // B with BF-row boxes, then with NBOX-row boxes
-            const cuuint32_t rows = static_cast<cuuint32_t>(v == 0 ? BF : NBOX);
-            CUtensorMap *mB = &maps[2 + 2 * v + h];
-            CUresult rb;
-            if (s > 1) {
-                const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(s),
-                                            static_cast<cuuint64_t>(L.n_k)};
-                const cuuint64_t strB[2] = {rowb, rowb * static_cast<cuuint64_t>(s)};
-                const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), 1, rows};
-                const cuuint32_t es3[3] = {1, 1, 1};
-                rb = encode(mB, dt, 3, bbases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            } else {
-                const cuuint64_t dimB[2] = {static_cast<cuuint64_t>(L.Kp), static_cast<cuuint64_t>(L.n_k)};
-                const cuuint64_t strB[1] = {rowb};
-                const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(L.bke), rows};
-                rb = encode(mB, dt, 2, bbases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            }
-            if (rb != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (B)");
-        }
-    }
+// The band operands are read as tile images by plain bulk copies, so a band
+// instance carries no tensor maps: its map slots are zeroed (only polyphase
+// instances, whose maps poly_setup encodes, touch them).
+int encode_maps(const GramLayout &, uint8_t *, int64_t, CUtensorMap *maps) {
+    std::memset(maps, 0, sizeof(CUtensorMap) * NMAPS);
     return TCORR_OK;
 }
 
@@ -1824,6 +1872,12 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
     ga.super_rows = L.super_rows;
     ga.super_cols = L.super_cols;
     supertile_env(&ga.super_rows, &ga.super_cols);
+    ga.xa_h = base + L.off_xh;
+    ga.xa_l = base + L.off_xl;
+    ga.xb_h = base + (L.cross ? L.off_bh : L.off_xh);
+    ga.xb_l = base + (L.cross ? L.off_bl : L.off_xl);
+    ga.nkp = L.nkp;
+    ga.rows = L.rows;
     return ga;
 }
 
@@ -1974,6 +2028,8 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
     ga.inv_scale_b = L.cross ? reinterpret_cast<const float *>(base + L.off_scale_b) : ga.inv_scale;
     ga.partial = reinterpret_cast<double *>(base + L.off_partial);
     ga.b3d = 2;
+    ga.xa_h = ga.xa_l = ga.xb_h = ga.xb_l = nullptr;
+    ga.nkp = ga.rows = 0;
     ga.sub_kb = L.sub_kb;
     ga.counter = reinterpret_cast<unsigned long long *>(base + L.off_counter);
     ga.mode = 1;
@@ -2352,7 +2408,7 @@ int gram_batch_run(const tcorr_instance *items, int count, int method, void *d_w
             if (split_class(spl[k]) != c) continue;
             SplitDesc q = spl[k];
             q.blk_begin = cls_blocks[c];
-            cls_blocks[c] += q.warp_mode ? ceil_div(q.T_pad, kWarpFrames) * q.n_groups : q.T_pad * q.n_groups;
+            cls_blocks[c] += q.warp_mode ? ceil_div(q.rows, kWarpFrames) * q.n_groups : q.rows * q.n_groups;
             spl_by_class.push_back(q);
         }
     }
