@@ -65,6 +65,7 @@ namespace {
 
 constexpr int BO = 128;             // origins per tile (MMA M)
 constexpr int BF = 192;             // frames per tile (MMA N)
+constexpr int POLY_L = 3 * BO;      // polyphase phases: 384 = 3 row tiles = 2 column tiles
 constexpr int STAGES = 5;
 constexpr int ROWB = 64;            // bytes of K per staged row = one 64B swizzle span
 constexpr int A_BYTES = BO * ROWB;  // 8 KB
@@ -214,13 +215,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int32_t c0,
-                                            int32_t c1, int32_t c2, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
         : "memory");
 }
 // Plain bulk copy global -> shared (contiguous bytes, 16-byte aligned).
@@ -559,7 +553,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             const uint32_t b_bytes = static_cast<uint32_t>(nbox * brows * ROWB);
             const uint32_t stage_tx = 2 * A_BYTES + 2 * b_bytes;
             if (b3d == 2) {
-                // polyphase: tensor maps over row-major (K, phase row, shifted copy) operands
+                // polyphase: tensor maps over row-major (K, copy * POLY_L + phase) operands
                 if (mp[0] != last_map) {      // new instance: bring its descriptors close to the TMA unit
                     for (int i = 0; i < NMAPS; ++i) prefetch_tensormap(mp[i]);
                     last_map = mp[0];
@@ -576,8 +570,8 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                     tma_load_2d(sbase + A_BYTES, mp[1], kx, ay, full_bar(st));
                     for (int j = 0; j < nbox; ++j) {
                         const uint32_t sh = sbase + 2 * A_BYTES + j * NBOX_BYTES, sl = sh + B_BYTES;
-                        tma_load_3d(sh, mbh, kx + bx, by + j * NBOX, bz, full_bar(st));
-                        tma_load_3d(sl, mbl, kx + bx, by + j * NBOX, bz, full_bar(st));
+                        tma_load_2d(sh, mbh, kx + bx, bz * POLY_L + by + j * NBOX, full_bar(st));
+                        tma_load_2d(sl, mbl, kx + bx, bz * POLY_L + by + j * NBOX, full_bar(st));
                     }
                     if (++st == STAGES) {
                         st = 0;
@@ -1306,7 +1300,6 @@ __global__ void __launch_bounds__(PFX_THREADS) s_prefix_batch_kernel(const PfxDe
 // coordinate) and q mod 8, served by one of 8 copies of Y pre-shifted by
 // 0..7 elements.  Each series occupies Pp >= P + nq slots of the contraction
 // so that shifted reads never reach the next series.
-constexpr int POLY_L = 3 * BO;       // 384 = 3 row tiles = 2 column tiles
 
 struct PolyPrepArgs {
     const float *X;
@@ -2000,13 +1993,13 @@ int poly_setup(int kind, const float *d_x, const GramLayout &L, uint8_t *base, d
                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase A)");
-        const cuuint64_t dimB[3] = {static_cast<cuuint64_t>(L.Kalloc), POLY_L, 8};
-        const cuuint64_t strB[2] = {rowb, rowb * POLY_L};
-        const cuuint32_t es3[3] = {1, 1, 1};
+        // the 8 shifted copies are consecutive blocks of POLY_L rows: one 2-D map,
+        // row = copy * POLY_L + phase (a 2-D box moves faster than a 3-D one)
+        const cuuint64_t dimB[2] = {static_cast<cuuint64_t>(L.Kalloc), 8 * POLY_L};
+        const cuuint64_t strB[1] = {rowb};
         for (int v = 0; v < 2; ++v) {          // B with BF-row boxes, then with NBOX-row boxes
-            const cuuint32_t boxB[3] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(v == 0 ? BF : NBOX),
-                                        1};
-            if (encode(&maps[2 + 2 * v + h], dt, 3, bbases[h], dimB, strB, boxB, es3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(L.bke), static_cast<cuuint32_t>(v == 0 ? BF : NBOX)};
+            if (encode(&maps[2 + 2 * v + h], dt, 2, bbases[h], dimB, strB, boxB, es2, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (polyphase B)");
