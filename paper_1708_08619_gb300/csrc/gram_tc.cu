@@ -746,16 +746,37 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 rs = (row < I.a_rows) ? isc[I.sa0 + row * I.sstr] : 1.f;
                 named_bar_sync(1, 32 * NEPI);
             }
+            // Diagonal sums of this warp's 32 x 96 block: entry (lane l, column jj)
+            // lies on diagonal d = jj - l in [-31, 95].  Lane L keeps the diagonals
+            // d = L - 32 + 32 k (k = 0..3); for each jj it takes the entry of lane
+            // (jj - L) mod 32 by a shuffle, whose diagonal is L - 32 + 32 k with
+            // k = floor((jj - L) / 32) + 1.  Each diagonal adds its entries in
+            // increasing jj, and the sums go to this warp's own slice of lagbuf.
             const int64_t mrow = I.moff - row;        // band offset / lag m = mrow + j
+            float dg0 = 0.f, dg1 = 0.f, dg2 = 0.f, dg3 = 0.f;
 #pragma unroll
             for (int jj = 0; jj < BF / 2; ++jj) {
                 const int j = (BF / 2) * half + jj;
                 const int64_t m = mrow + j;
+                float val = 0.f;
                 if (m >= 0 && m <= I.m_max && row < I.a_rows) {
-                    float val = acc2[jj];
+                    val = acc2[jj];
                     if (PREC == P_FP16) val = (val * rs) * cs[j];
-                    atomicAdd(&lb[j - row + (BO - 1)], val);
                 }
+                const float got = __shfl_sync(0xffffffffu, val, (jj - lane) & 31);
+                const int k = (jj - lane + 32) >> 5;
+                dg0 += k == 0 ? got : 0.f;
+                dg1 += k == 1 ? got : 0.f;
+                dg2 += k == 2 ? got : 0.f;
+                dg3 += k == 3 ? got : 0.f;
+            }
+            {
+                // diagonal d of this block is window slot d + 96 half - 32 q + BO - 1 (0 .. 318)
+                float *lw = lb + (BF / 2) * half - 32 * q + (BO - 1) + lane;
+                if (lane > 0) lw[-32] = dg0;      // lane 0: d = -32 holds no entry
+                lw[0] = dg1;
+                lw[32] = dg2;
+                lw[64] = dg3;
             }
             named_bar_sync(1, 32 * NEPI);
             for (int w = et; w < WPG; w += 32 * NEPI) {
