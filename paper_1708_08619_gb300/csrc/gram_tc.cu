@@ -127,6 +127,14 @@ void supertile_env(int64_t *rows, int64_t *cols) {
     }
 }
 
+// Band contraction on CTA pairs (gram_pair_kernel) for single instances;
+// TCORR_PAIR=0 / 1 overrides the default.
+constexpr bool kPairDefault = false;
+bool pair_enabled() {
+    if (const char *e = std::getenv("TCORR_PAIR")) return std::strcmp(e, "0") != 0;
+    return kPairDefault;
+}
+
 
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -294,6 +302,79 @@ __device__ __forceinline__ void named_bar_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// ---- CTA-pair (cta_group::2) helpers: a cluster of two CTAs on one TPC
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// The address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u64(uint32_t cluster_addr, int64_t v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait with cluster-scope acquire (arrivals may come from the peer CTA).
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag) return false;
+            const unsigned long long now = globaltimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitNs) {
+                atomicExch(&g_status, static_cast<unsigned int>(TCORR_ETIMEOUT));
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+// Arrive on barrier `bar` (same offset) in every CTA of `mask` when the MMAs
+// this thread issued so far have completed.
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(mask)
+                 : "memory");
+}
+template <int PREC>
+__device__ __forceinline__ void tc_mma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (PREC == P_TF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
 // Shared-memory matrix descriptor for a K-major tile with 64-byte rows and the
 // 64B swizzle: 8-row groups are 512 bytes apart (stride byte offset), the
 // leading byte offset is unused for this layout, version field = 1.
@@ -414,6 +495,56 @@ __device__ __forceinline__ Item decode_item(const GramArgs &a, int64_t item) {
         I.empty = (I.moff + BF - 1 < 0) || (I.moff - (BO - 1) > a.tau_max) || (I.kb0 >= I.kb1);
         I.ncol = item_ncol(I.moff, I.m_max);
     }
+    return I;
+}
+
+// Band item of a CTA pair (cta_group::2): row tiles 2 rp (rank 0) and
+// 2 rp + 1 (rank 1) against one column tile of frames k0 = 2 rp BO + c BF,
+// one M = 256 product whose B rows (frames) are split between the two CTAs:
+// rank 0 loads rows k0 .. k0 + ncol/2 - 1, rank 1 the next ncol/2.  Each CTA
+// keeps its own 128 x ncol accumulator, whose entry (i, j) holds lag
+// m = moff + j - i with moff = c BF - rank BO.  Pair items are claimed in
+// supertile order over (pair row, column); emptiness and ncol are decided for
+// the pair, so both CTAs agree on them.  The number of row tiles is even in a
+// pair layout (a last odd row tile gets a partner whose origins are all past
+// the last origin and are masked), and n_cols covers the lags of both ranks.
+__device__ __forceinline__ Item decode_pair(const GramArgs &a, int64_t item, int cr) {
+    Item I;
+    const int64_t n_prow = a.n_rows >> 1;
+    const int64_t per = n_prow * a.n_cols;
+    const int64_t gr = item / per;
+    int64_t u = item - gr * per;
+    const int64_t srows = a.super_rows >= 2 ? a.super_rows / 2 : 1;
+    const int64_t cs = a.n_cols < a.super_cols ? a.n_cols : a.super_cols;
+    const int64_t rb = u / (srows * a.n_cols);
+    u -= rb * srows * a.n_cols;
+    const int64_t rcount = min(srows, n_prow - rb * srows);
+    const int64_t cb = u / (rcount * cs);
+    u -= cb * rcount * cs;
+    const int64_t ccount = min(cs, a.n_cols - cb * cs);
+    const int64_t rp = rb * srows + u / ccount;
+    const int64_t c = cb * cs + u % ccount;
+    const int64_t r = 2 * rp + cr;
+    I.canon = (gr * a.n_rows + r) * a.n_cols + c;
+    I.rho = gr % a.n_res;
+    const int64_t g = gr / a.n_res;
+    const int64_t o0 = r * BO, k0 = 2 * rp * BO + c * BF;
+    I.a_y = o0;
+    I.b_x = 0;
+    I.b_z = I.rho;
+    I.moff = k0 - o0;
+    I.m_max = (a.tau_max - I.rho) / a.s;
+    I.sa0 = o0 * a.s;
+    I.sb0 = I.rho + k0 * a.s;
+    I.sstr = a.s;
+    I.a_rows = a.n_orig - o0;
+    const int64_t n_rho = n_frames_res(a.T, a.s, I.rho);
+    I.kb0 = g * a.kb_per_item;
+    I.kb1 = min(a.kb_total, I.kb0 + a.kb_per_item);
+    I.empty = (c * BF - 2 * BO + 1 > I.m_max) || (k0 >= n_rho) || (I.kb0 >= I.kb1);
+    const int64_t need = I.m_max - c * BF + 2 * BO;      // columns that can hold a kept lag, either rank
+    I.ncol = need >= BF ? BF : (need <= 32 ? 32 : static_cast<int>((need + 31) & ~int64_t(31)));
+    I.b_y = k0 + cr * (I.ncol / 2);
     return I;
 }
 
@@ -826,6 +957,342 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_band_batch_kernel(const __gr
 // ------------------------------------------------------------------ prep
 // One block per padded frame row t.  x = X[t] - X[m] (MSD, m the middle frame) or X[t] (ACF);
 // FP16 rows are scaled by 2^e_t with e_t chosen so max |x| * 2^e_t < 2^14.
+// ---------------------------------------------------- CTA-pair band kernel
+// The band contraction on CTA pairs (cta_group::2, clusters of two CTAs on one
+// TPC): each pair item is one M = 256 product (the two CTAs' row tiles) over
+// one column tile whose B rows are split between the CTAs, so each CTA loads
+// its A tile and half of B per K-block: 28 KB instead of 40 KB.  Roles per
+// CTA: warp 0 lane 0 loads the CTA's operands (the leader, rank 0, also claims
+// the items and publishes them to both CTAs); warp 1 lane 0 issues the MMAs in
+// the leader and, in the peer, relays each filled stage to the leader's full
+// barrier (a bulk copy completes on a barrier of its own CTA); warps 2..9 are
+// the epilogue of the CTA's own accumulator.  Leader barriers count the peer's
+// arrivals (full: 2, tempty: 2 x 8 warps, item slots: 3 + 2 x 8); commits go
+// to both CTAs by multicast.  Every wait is bounded as in gram_body.
+constexpr int STAGES_P = 7;
+constexpr int BH_BYTES = (BF / 2) * ROWB;                    // half of a B tile, 6 KB
+constexpr int STAGE_BYTES_P = 2 * A_BYTES + 2 * BH_BYTES;     // 28 KB
+constexpr size_t SMEM_STAGES_P = size_t(STAGES_P) * STAGE_BYTES_P;
+constexpr size_t SMEM_TOTAL_P = 1024 + SMEM_STAGES_P + SMEM_LAG + SMEM_CS + SMEM_BAR + 16 + IQ * 8;
+static_assert(SMEM_TOTAL_P <= 227 * 1024, "pair kernel shared memory");
+static_assert(2 * STAGES_P + 5 + 2 * IQ <= 32, "pair kernel barriers");
+
+template <int PREC, bool X4>
+__device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *stages = smem;
+    float *lagbuf = reinterpret_cast<float *>(smem + SMEM_STAGES_P);            // [NEPI][WPG]
+    float *cs = reinterpret_cast<float *>(smem + SMEM_STAGES_P + SMEM_LAG);     // [BF]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SMEM_STAGES_P + SMEM_LAG + SMEM_CS);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 32);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int64_t *item_q = reinterpret_cast<volatile int64_t *>(tmem_slot + 4);   // [IQ]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t cr = cluster_rank();
+    const bool leader = cr == 0;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int st) { return bar0 + 8u * st; };
+    auto empty_bar = [&](int st) { return bar0 + 8u * (STAGES_P + st); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES_P + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES_P + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES_P + 4);
+    auto iq_full_bar = [&](int q) { return bar0 + 8u * (2 * STAGES_P + 5 + q); };
+    auto iq_empty_bar = [&](int q) { return bar0 + 8u * (2 * STAGES_P + 5 + IQ + q); };
+    // arrive on a barrier of the leader: locally in the leader, remotely from the peer
+    auto arrive_leader = [&](uint32_t bar) {
+        if (leader) mbar_arrive(bar);
+        else mbar_arrive_cluster(map_to_rank(bar, 0));
+    };
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES_P; ++st) {
+            mbar_init(full_bar(st), leader ? 2 : 1);
+            mbar_init(empty_bar(st), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), 2 * NEPI);
+        }
+        mbar_init(drain_bar, 1);
+        for (int q = 0; q < IQ; ++q) {
+            mbar_init(iq_full_bar(q), 1);
+            mbar_init(iq_empty_bar(q), 3 + 2 * NEPI);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp >= 2) {
+        for (int i = threadIdx.x - 64; i < NEPI * WPG; i += 32 * NEPI) lagbuf[i] = 0.f;
+    }
+    if (warp == 1) {   // one allocation for the pair, made by one warp of each CTA together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();   // both CTAs' barriers exist before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int64_t n_items = a.n_items;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        int st = 0;
+        uint32_t ph = 0;
+        unsigned long long *ctr = a.counter;
+        for (uint32_t it = 0;; ++it) {
+            const int qs = it % IQ;
+            int64_t item;
+            if (leader) {   // claim the next pair item and publish it to both CTAs
+                if (!mbar_wait_cluster(iq_empty_bar(qs), ((it / IQ) & 1u) ^ 1u, abort_flag)) break;
+                const int64_t claimed = static_cast<int64_t>(atomicAdd(ctr, 1ull));
+                item = claimed < n_items ? claimed : -1;
+                item_q[qs] = item;
+                st_cluster_u64(map_to_rank(smem_u32(const_cast<int64_t *>(&item_q[qs])), 1), item);
+                mbar_arrive(iq_full_bar(qs));
+                mbar_arrive_cluster(map_to_rank(iq_full_bar(qs), 1));
+            } else {
+                if (!mbar_wait_cluster(iq_full_bar(qs), (it / IQ) & 1u, abort_flag)) break;
+                item = item_q[qs];
+                mbar_arrive_cluster(map_to_rank(iq_empty_bar(qs), 0));
+            }
+            if (item < 0) break;
+            const Item I = decode_pair(a, item, static_cast<int>(cr));
+            if (I.empty) continue;
+            const uint32_t b_bytes = static_cast<uint32_t>(I.ncol / 2) * ROWB;
+            const uint32_t stage_tx = 2 * A_BYTES + 2 * b_bytes;
+            const int64_t ra = I.a_y, rb = I.b_z * a.nkp + I.b_y;
+            for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
+                if (!mbar_wait_cluster(empty_bar(st), ph ^ 1u, abort_flag)) goto pair_producer_done;
+                mbar_arrive_expect_tx(full_bar(st), stage_tx);
+                const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES_P);
+                const int64_t plane = kb * a.rows;
+                const int64_t oa = (plane + ra) * ROWB, ob = (plane + rb) * ROWB;
+                bulk_load(sbase, a.xa_h + oa, A_BYTES, full_bar(st));
+                bulk_load(sbase + A_BYTES, a.xa_l + oa, A_BYTES, full_bar(st));
+                bulk_load(sbase + 2 * A_BYTES, a.xb_h + ob, b_bytes, full_bar(st));
+                bulk_load(sbase + 2 * A_BYTES + BH_BYTES, a.xb_l + ob, b_bytes, full_bar(st));
+                if (++st == STAGES_P) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+    pair_producer_done:;
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------- MMA (leader) / relay (peer)
+        constexpr uint32_t idesc = (make_idesc<PREC>() & ~(0x1Fu << 24)) | (static_cast<uint32_t>((2 * BO) >> 4) << 24);
+        int st = 0;
+        uint32_t ph = 0, chain = 0;
+        bool issued = false, aborted = false;
+        for (uint32_t it = 0; !aborted; ++it) {
+            const int qs = it % IQ;
+            if (!mbar_wait_cluster(iq_full_bar(qs), (it / IQ) & 1u, abort_flag)) break;
+            const int64_t item = item_q[qs];
+            arrive_leader(iq_empty_bar(qs));
+            if (item < 0) break;
+            const Item I = decode_pair(a, item, static_cast<int>(cr));
+            if (I.empty) continue;
+            if (!leader) {
+                for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
+                    if (!mbar_wait_cluster(full_bar(st), ph, abort_flag)) {
+                        aborted = true;
+                        break;
+                    }
+                    mbar_arrive_cluster(map_to_rank(full_bar(st), 0));
+                    if (++st == STAGES_P) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+                continue;
+            }
+            const uint32_t idesc_i = (idesc & ~(0x3Fu << 17)) | (static_cast<uint32_t>(I.ncol >> 3) << 17);
+            const int64_t sub_kb = a.sub_kb;
+            for (int64_t kc = I.kb0; kc < I.kb1 && !aborted; kc += sub_kb) {
+                const int64_t kc1 = min(I.kb1, kc + sub_kb);
+                const int b = chain & 1;
+                if (!mbar_wait_cluster(tempty_bar(b), ((chain >> 1) & 1u) ^ 1u, abort_flag)) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + static_cast<uint32_t>(b * BF);
+                for (int64_t kb = kc; kb < kc1; ++kb) {
+                    if (!mbar_wait_cluster(full_bar(st), ph, abort_flag)) {
+                        aborted = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sA = smem_u32(stages + size_t(st) * STAGE_BYTES_P);
+                    const uint64_t dAh = smem_desc_sw64(sA);
+                    const uint64_t dAl = smem_desc_sw64(sA + A_BYTES);
+                    const uint64_t dBh = smem_desc_sw64(sA + 2 * A_BYTES);
+                    const uint64_t dBl = smem_desc_sw64(sA + 2 * A_BYTES + BH_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t adv = static_cast<uint64_t>(ks * 2);
+                        const uint32_t acc = (kb != kc || ks != 0) ? 1u : 0u;
+                        tc_mma_pair<PREC>(d, dAh + adv, dBh + adv, idesc_i, acc);
+                        tc_mma_pair<PREC>(d, dAh + adv, dBl + adv, idesc_i, 1u);
+                        tc_mma_pair<PREC>(d, dAl + adv, dBh + adv, idesc_i, 1u);
+                        if (X4) tc_mma_pair<PREC>(d, dAl + adv, dBl + adv, idesc_i, 1u);
+                    }
+                    issued = true;
+                    tc_commit_pair(empty_bar(st), 3);
+                    if (++st == STAGES_P) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (aborted) break;
+                tc_commit_pair(tfull_bar(b), 3);
+                ++chain;
+            }
+        }
+        if (leader && issued) {   // wait (bounded) until every MMA issued has completed
+            tc_commit_pair(drain_bar, 1);
+            int dummy = 0;
+            volatile int *never = &dummy;
+            mbar_wait_cluster(drain_bar, 0u, never);
+        }
+    }
+    else if (warp >= 2) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;     // which 96 accumulator columns
+        const int row = 32 * q + lane;        // accumulator row = origin o0 + row
+        const int et = threadIdx.x - 64;
+        float *lb = lagbuf + (warp - 2) * WPG;
+        uint32_t chain = 0;
+        bool aborted = false;
+        for (uint32_t it = 0;; ++it) {
+            const int qs = it % IQ;
+            if (!mbar_wait_cluster(iq_full_bar(qs), (it / IQ) & 1u, abort_flag)) break;
+            const int64_t item = item_q[qs];
+            __syncwarp();
+            if (lane == 0) arrive_leader(iq_empty_bar(qs));
+            if (item < 0) break;
+            int64_t kb0, kb1;
+            int ncol;
+            {
+                const Item I0 = decode_pair(a, item, static_cast<int>(cr));
+                if (I0.empty) {
+                    double *outp0 = a.partial + I0.canon * WPG;
+                    for (int w = et; w < WPG; w += 32 * NEPI)
+                        if (TCORR_IN_BOUNDS(I0.canon * WPG + w, a.partial_elems, a.dbg_status)) outp0[w] = 0.0;
+                    continue;
+                }
+                kb0 = I0.kb0;
+                kb1 = I0.kb1;
+                ncol = I0.ncol;
+            }
+            const int hcols = ncol - (BF / 2) * half;
+            const int64_t sub_kb = a.sub_kb;
+            float acc2[BF / 2];
+#pragma unroll
+            for (int j = 0; j < BF / 2; ++j) acc2[j] = 0.f;
+            for (int64_t kc = kb0; kc < kb1; kc += sub_kb) {
+                const int b = chain & 1;
+                if (!mbar_wait_cluster(tfull_bar(b), (chain >> 1) & 1u, abort_flag)) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + (static_cast<uint32_t>(32 * q) << 16) +
+                                       static_cast<uint32_t>(b * BF + (BF / 2) * half);
+                if (hcols > 0) {
+                    uint32_t v[64];
+                    tmem_ld64(tbase, v);
+#pragma unroll
+                    for (int jj = 0; jj < 64; ++jj) acc2[jj] += __uint_as_float(v[jj]);
+                }
+                if (hcols > 64) {
+                    uint32_t v[32];
+                    tmem_ld32(tbase + 64, v);
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) acc2[64 + jj] += __uint_as_float(v[jj]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) arrive_leader(tempty_bar(b));
+                ++chain;
+            }
+            if (aborted) break;
+            const Item I = decode_pair(a, item, static_cast<int>(cr));
+            double *outp = a.partial + I.canon * WPG;
+            float rs = 1.f;
+            if (PREC == P_FP16) {
+                const int64_t gofs = (I.kb0 / a.kb_per_item) * a.scale_stride;
+                const float *isc = a.inv_scale + gofs, *iscb = a.inv_scale_b + gofs;
+                for (int j = et; j < BF; j += 32 * NEPI) {
+                    const int64_t f = I.sb0 + j * I.sstr;
+                    cs[j] = f < a.T ? iscb[f] : 1.f;
+                }
+                rs = (row < I.a_rows) ? isc[I.sa0 + row * I.sstr] : 1.f;
+                named_bar_sync(1, 32 * NEPI);
+            }
+            // diagonal sums by warp shuffles, as in gram_body
+            const int64_t mrow = I.moff - row;
+            float dg0 = 0.f, dg1 = 0.f, dg2 = 0.f, dg3 = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < BF / 2; ++jj) {
+                const int j = (BF / 2) * half + jj;
+                const int64_t m = mrow + j;
+                float val = 0.f;
+                if (m >= 0 && m <= I.m_max && row < I.a_rows) {
+                    val = acc2[jj];
+                    if (PREC == P_FP16) val = (val * rs) * cs[j];
+                }
+                const float got = __shfl_sync(0xffffffffu, val, (jj - lane) & 31);
+                const int k = (jj - lane + 32) >> 5;
+                dg0 += k == 0 ? got : 0.f;
+                dg1 += k == 1 ? got : 0.f;
+                dg2 += k == 2 ? got : 0.f;
+                dg3 += k == 3 ? got : 0.f;
+            }
+            {
+                float *lw = lb + (BF / 2) * half - 32 * q + (BO - 1) + lane;
+                if (lane > 0) lw[-32] = dg0;
+                lw[0] = dg1;
+                lw[32] = dg2;
+                lw[64] = dg3;
+            }
+            named_bar_sync(1, 32 * NEPI);
+            for (int w = et; w < WPG; w += 32 * NEPI) {
+                float sum = 0.f;
+#pragma unroll
+                for (int e = 0; e < NEPI; ++e) {
+                    sum += lagbuf[e * WPG + w];
+                    lagbuf[e * WPG + w] = 0.f;
+                }
+                if (TCORR_IN_BOUNDS(I.canon * WPG + w, a.partial_elems, a.dbg_status)) outp[w] = static_cast<double>(sum);
+            }
+            named_bar_sync(1, 32 * NEPI);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();   // no remote arrival or MMA into this CTA's memory after this point
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+template <int PREC, bool X4>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    gram_pair_kernel(const __grid_constant__ GramArgs a) {
+    gram_pair_body<PREC, X4>(a);
+}
+
 constexpr int PREP_THREADS = 256;
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -1548,7 +2015,8 @@ struct GramLayout {
     int64_t Kp, T_pad, n_k, esize, bke, pstride, kseg;
     int sub_kb;
     int super_rows = kDefaultSuperRows, super_cols = kDefaultSuperCols;   // band claim order
-    int64_t nkp = 0, rows = 0;      // band tile images: rows per residue (>= n_k + BF) and per plane (s nkp)
+    int64_t nkp = 0, rows = 0;      // band tile images: rows per residue (>= n_k + 2 BO) and per plane (s nkp)
+    bool pair = false;              // band on CTA pairs (gram_pair_kernel)
     bool poly;                      // polyphase layout (small K, stride 1)
     int64_t P, Pp, nq, Kprime, Kalloc;
     size_t off_xh, off_xl, off_scale, off_S, off_prefix, off_partial, off_counter, total;
@@ -1638,7 +2106,7 @@ bool make_poly_layout(int64_t T, int64_t N, int64_t tau_max, int method, int kin
 // w != nullptr: one window of a streamed trajectory (band form only: the
 // polyphase contraction cannot stop origins at a cap).
 bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, int kind, GramLayout *L,
-                 const Window *w = nullptr) {
+                 const Window *w = nullptr, bool allow_pair = false) {
     if (!method_prec(method, &L->prec, &L->x4)) return false;
     L->esize = L->prec == P_TF32 ? 4 : 2;
     L->bke = L->prec == P_TF32 ? 16 : 32;
@@ -1648,7 +2116,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     if (L->poly) return make_poly_layout(T, N, tau_max, method, kind, L);
     L->Kp = ceil_div(K, 64) * 64;
     L->n_k = ceil_div(T, s);
-    L->nkp = ceil_div(L->n_k + BF, 8) * 8;   // a tile starting at a real row never leaves its residue
+    L->nkp = ceil_div(L->n_k + 2 * BO, 8) * 8;   // a tile starting at a real row never leaves its residue
     L->rows = s * L->nkp;
     L->T_pad = L->n_k * s;           // rows rho + k s for every rho < s, k < n_k exist
     // kseg / sub_kb: tuning override, then environment, then tuned cache, then defaults
@@ -1672,6 +2140,12 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->p = make_band_plan(T, N, tau_max, s, BO, BF, L->kseg, 1);
     if (w) cap_origins(&L->p, w->orig_cap);
     L->p.WP = WPG;
+    L->pair = allow_pair && pair_enabled();
+    if (L->pair) {   // an even number of row tiles; columns for the lags of both ranks of a pair
+        L->p.pair = 1;
+        L->p.n_rows = ceil_div(L->p.n_rows, 2) * 2;
+        L->p.n_cols = ceil_div(2 * BO + L->p.m_max0, BF);
+    }
     // one K group per segment of kseg elements
     const int64_t kb_total = ceil_div(K, L->bke);
     const int64_t kb_per_item = L->kseg / L->bke;
@@ -1741,6 +2215,17 @@ cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, c
     prof_begin(kind, st);
     gram_band_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
                                                                       maps[5], ga);
+    prof_end(st);
+    return cudaGetLastError();
+}
+
+template <int PREC, bool X4>
+cudaError_t launch_gram_pair(const GramArgs &ga, int grid, cudaStream_t st, int kind) {
+    cudaError_t e = cudaFuncSetAttribute(gram_pair_kernel<PREC, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(SMEM_TOTAL_P));
+    if (e != cudaSuccess) return e;
+    prof_begin(kind, st);
+    gram_pair_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL_P, st>>>(ga);
     prof_end(st);
     return cudaGetLastError();
 }
@@ -1867,7 +2352,7 @@ GramArgs gram_args(const GramLayout &L, uint8_t *base, int64_t T, int64_t N, int
     ga.n_res = L.p.n_res;
     ga.n_rows = L.p.n_rows;
     ga.n_cols = L.p.n_cols;
-    ga.n_items = L.p.n_items;
+    ga.n_items = L.pair ? L.p.n_items / 2 : L.p.n_items;   // pair items cover two row tiles
     ga.kb_total = ceil_div(3 * N, L.bke);
     ga.kb_per_item = L.kseg / L.bke;
     ga.inv_scale = reinterpret_cast<const float *>(base + L.off_scale);
@@ -2145,14 +2630,14 @@ int poly_run(int kind, const float *d_x, const GramLayout &L, uint8_t *base, dou
 size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, const Window *w,
                            int kind) {
     GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, kind, &L, w)) return 0;
+    if (!make_layout(T, N, tau_max, s, method, kind, &L, w, true)) return 0;
     size_t need = L.total;
     if (!w && tune_mode() != 0) {
         const TuneChoice shortest{tune_min_kseg(), 0};
         const TuneChoice *prev = get_tune_override();
         set_tune_override(&shortest);
         GramLayout Ls;
-        if (make_layout(T, N, tau_max, s, method, kind, &Ls) && Ls.total > need) need = Ls.total;
+        if (make_layout(T, N, tau_max, s, method, kind, &Ls, nullptr, true) && Ls.total > need) need = Ls.total;
         set_tune_override(prev);
     }
     return need;
@@ -2184,7 +2669,7 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
                   double *d_out, void *d_ws, size_t ws_bytes, cudaStream_t st, const Window *w = nullptr,
                   const float *d_y = nullptr) {
     GramLayout L;
-    if (!make_layout(T, N, tau_max, s, method, kind, &L, w)) return TCORR_EUNSUPPORTED;
+    if (!make_layout(T, N, tau_max, s, method, kind, &L, w, true)) return TCORR_EUNSUPPORTED;
     if (ws_bytes < L.total || !d_ws) return TCORR_EWORKSPACE;
     int num_sms = 0;
     if (!device_is_sm103(&num_sms)) return TCORR_EUNSUPPORTED;
@@ -2222,6 +2707,20 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     const GramArgs ga = gram_args(L, ws, T, N, tau_max, s);
     e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "work-item counter reset");
+    if (L.pair) {   // one cluster of two CTAs per TPC
+        const int64_t pairs = num_sms / 2;
+        const int grid = 2 * static_cast<int>(ga.n_items < pairs ? ga.n_items : pairs);
+        switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
+            case P_FP16 * 2: e = launch_gram_pair<P_FP16, false>(ga, grid, st, kind & 1); break;
+            case P_BF16 * 2: e = launch_gram_pair<P_BF16, false>(ga, grid, st, kind & 1); break;
+            case P_BF16 * 2 + 1: e = launch_gram_pair<P_BF16, true>(ga, grid, st, kind & 1); break;
+            default: e = launch_gram_pair<P_TF32, false>(ga, grid, st, kind & 1); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gram_pair_kernel launch");
+        e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st, w);
+        if (e != cudaSuccess) return cuda_fail(e, "lag_reduce launch");
+        return TCORR_OK;
+    }
     const int grid = static_cast<int>(L.p.n_items < num_sms ? L.p.n_items : num_sms);
     switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
         case P_FP16 * 2: e = launch_gram<P_FP16, false>(maps, ga, grid, st, kind & 1); break;

@@ -22,24 +22,26 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // One warp per lag.  Lane l sums terms l, l+32, ... in order; the lanes are
 // then combined by a fixed butterfly, so the result does not depend on timing.
-__device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t tau, int lane) {
-    const int64_t rho = tau % a.s, m = tau / a.s;
-    const int64_t c_lo = m / a.BF;
-    int64_t c_hi = (m + a.BO - 1) / a.BF;
+// The lane's share of the window terms of lag m' = m + radd BO over row
+// tiles rr rmul + radd (rr < nrow): term t = (gg, rr, cc) with cc fastest; the
+// lane's first term is decoded once and each step of 32 terms is added as
+// mixed-radix carries (no 64-bit division in the loop; a fixed order).
+__device__ __forceinline__ double lag_terms(const LagReduceDesc &a, int64_t rho, int64_t mp, int64_t nrow,
+                                            int64_t rmul, int64_t radd, int lane) {
+    const int64_t c_lo = mp / a.BF;
+    int64_t c_hi = (mp + a.BO - 1) / a.BF;
     if (c_hi > a.n_cols - 1) c_hi = a.n_cols - 1;
     const int64_t ncs = c_hi - c_lo + 1;
-    const int64_t nterm = a.n_groups * a.n_rows * ncs;
     double sum = 0.0;
-    // term t = (gg, rr, cc) with cc fastest; the lane's first term is decoded
-    // once and each step of 32 terms is added as mixed-radix carries (no
-    // 64-bit division in the loop; the same terms in the same order)
+    if (ncs <= 0 || nrow <= 0) return sum;
+    const int64_t nterm = a.n_groups * nrow * ncs;
     int64_t cc = lane % ncs, q = lane / ncs;
-    int64_t rr = q % a.n_rows, gg = q / a.n_rows;
+    int64_t rr = q % nrow, gg = q / nrow;
     const int64_t dc = 32 % ncs, dq = 32 / ncs;
     for (int64_t t = lane; t < nterm; t += 32) {
         const int64_t c = c_lo + cc;
-        const int64_t item = ((gg * a.n_res + rho) * a.n_rows + rr) * a.n_cols + c;
-        const int64_t w = m - c * a.BF + a.BO - 1;
+        const int64_t item = ((gg * a.n_res + rho) * a.n_rows + rr * rmul + radd) * a.n_cols + c;
+        const int64_t w = mp - c * a.BF + a.BO - 1;
         const int64_t at = item * a.WP + w;
         if (TCORR_IN_BOUNDS(at, a.partial_elems, a.dbg_status)) sum += a.partial[at];
         cc += dc;
@@ -49,10 +51,24 @@ __device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t 
             ++carry;
         }
         rr += carry;
-        while (rr >= a.n_rows) {
-            rr -= a.n_rows;
+        while (rr >= nrow) {
+            rr -= nrow;
             ++gg;
         }
+    }
+    return sum;
+}
+
+__device__ __forceinline__ void lag_reduce_body(const LagReduceDesc &a, int64_t tau, int lane) {
+    const int64_t rho = tau % a.s, m = tau / a.s;
+    double sum;
+    if (!a.pair) {
+        sum = lag_terms(a, rho, m, a.n_rows, 1, 0, lane);
+    } else {
+        // CTA-pair tiling: even row tiles as in the plain tiling, odd ones hold lag m
+        // at the window place of m + BO
+        sum = lag_terms(a, rho, m, a.n_rows / 2, 2, 0, lane);
+        sum += lag_terms(a, rho, m + a.BO, a.n_rows / 2, 2, 1, lane);
     }
     const double D = warp_sum(sum);
     if (lane == 0) {
@@ -99,12 +115,22 @@ __global__ void lag_reduce_batch_kernel(const LagReduceDesc *__restrict__ d, int
 
 constexpr int kChunkBytes = 28672;
 struct ByteChunk {
+    alignas(16) uint8_t bytes[kChunkBytes];
     uint32_t n;
-    uint8_t bytes[kChunkBytes];
 };
 
+// Parameter memory serves one address per lane at a time, so the chunk is
+// read in 16-byte words where the destination allows it.
 __global__ void write_bytes_kernel(uint8_t *dst, const __grid_constant__ ByteChunk c) {
-    for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.bytes[i];
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        const uint32_t n16 = c.n / 16;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(c.bytes);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) d4[i] = s4[i];
+        done = n16 * 16;
+    }
+    for (uint32_t i = done + threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.bytes[i];
 }
 
 // Running trapezoid, I(k) = I(k-1) + dt (c[k-1] + c[k]) / 2, spread over
@@ -316,6 +342,7 @@ LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const Fi
     a.lag_begin = lag_begin;
     a.n_orig = p.n_orig;
     a.accumulate = 0;
+    a.pair = p.pair;
     return a;
 }
 

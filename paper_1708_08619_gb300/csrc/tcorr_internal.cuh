@@ -44,6 +44,7 @@ struct BandPlan {
     int64_t segs_per_item;    // segments one work item walks
     int64_t n_groups;         // K groups: ceil(ceil(K/kseg)/segs_per_item)
     int64_t n_items;          // n_groups * n_res * n_rows * n_cols
+    int pair = 0;             // CTA-pair tiling: odd row tiles r hold lags m = c BF - BO + j - i
 };
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -226,6 +227,7 @@ struct LagReduceDesc {
     int64_t lag_begin;        // batch: first global lag of this instance
     int64_t n_orig;           // origins that start pairs (n_o(tau) is capped by it)
     int accumulate;           // 1: out[tau] += numerator (streamed windows)
+    int pair;                 // CTA-pair tiling (see BandPlan::pair)
 };
 LagReduceDesc lag_reduce_desc(const BandPlan &p, const double *partial, const FinalizeArgs &fa,
                               double *d_out, int64_t lag_begin);
