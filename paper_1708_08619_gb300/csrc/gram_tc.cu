@@ -351,6 +351,15 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
         }
     }
 }
+// Tensor copy into this CTA's shared memory that completes on a barrier of
+// either CTA of the pair (cluster address `bar`).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, int32_t c0, int32_t c1,
+                                                 uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
 // Arrive on barrier `bar` (same offset) in every CTA of `mask` when the MMAs
 // this thread issued so far have completed.
 __device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t mask) {
@@ -963,12 +972,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_band_batch_kernel(const __gr
 // one column tile whose B rows are split between the CTAs, so each CTA loads
 // its A tile and half of B per K-block: 28 KB instead of 40 KB.  Roles per
 // CTA: warp 0 lane 0 loads the CTA's operands (the leader, rank 0, also claims
-// the items and publishes them to both CTAs); warp 1 lane 0 issues the MMAs in
-// the leader and, in the peer, relays each filled stage to the leader's full
-// barrier (a bulk copy completes on a barrier of its own CTA); warps 2..9 are
-// the epilogue of the CTA's own accumulator.  Leader barriers count the peer's
-// arrivals (full: 2, tempty: 2 x 8 warps, item slots: 3 + 2 x 8); commits go
-// to both CTAs by multicast.  Every wait is bounded as in gram_body.
+// the items and publishes them to both CTAs); warp 1 lane 0 of the leader
+// issues the MMAs; warps 2..9 are the epilogue of the CTA's own accumulator.
+// The operand tiles are read as 2-D views of their tile images (rows of 512
+// bytes) by tensor copies that complete on the leader's full barrier, so one
+// barrier sees both CTAs' bytes.  Leader barriers count the peer's arrivals
+// (tempty: 2 x 8 warps, item slots: 2 + 2 x 8); commits go to both CTAs by
+// multicast.  Every wait is bounded as in gram_body.
 constexpr int STAGES_P = 7;
 constexpr int BH_BYTES = (BF / 2) * ROWB;                    // half of a B tile, 6 KB
 constexpr int STAGE_BYTES_P = 2 * A_BYTES + 2 * BH_BYTES;     // 28 KB
@@ -978,7 +988,7 @@ static_assert(SMEM_TOTAL_P <= 227 * 1024, "pair kernel shared memory");
 static_assert(2 * STAGES_P + 5 + 2 * IQ <= 32, "pair kernel barriers");
 
 template <int PREC, bool X4>
-__device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
+__device__ __forceinline__ void gram_pair_body(const GramArgs &a, const CUtensorMap *const *mp) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *stages = smem;
@@ -1008,7 +1018,7 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES_P; ++st) {
-            mbar_init(full_bar(st), leader ? 2 : 1);
+            mbar_init(full_bar(st), 1);
             mbar_init(empty_bar(st), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -1018,7 +1028,7 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
         mbar_init(drain_bar, 1);
         for (int q = 0; q < IQ; ++q) {
             mbar_init(iq_full_bar(q), 1);
-            mbar_init(iq_empty_bar(q), 3 + 2 * NEPI);
+            mbar_init(iq_empty_bar(q), 2 + 2 * NEPI);
         }
         *abort_flag = 0;
         fence_barrier_init();
@@ -1064,19 +1074,28 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
             if (item < 0) break;
             const Item I = decode_pair(a, item, static_cast<int>(cr));
             if (I.empty) continue;
+            // each operand tile is a contiguous tile image, read through a 2-D view of
+            // 512-byte rows (8 tile rows each); every copy of both CTAs completes on
+            // the leader's full barrier, whose expected bytes count both CTAs
             const uint32_t b_bytes = static_cast<uint32_t>(I.ncol / 2) * ROWB;
-            const uint32_t stage_tx = 2 * A_BYTES + 2 * b_bytes;
+            const uint32_t pair_tx = 2 * (2 * A_BYTES + 2 * b_bytes);
+            const bool narrow = I.ncol < BF;
+            const int nbox = narrow ? I.ncol / 32 : 1;          // narrow B half: 1 KB boxes
+            const CUtensorMap *mbh = narrow ? mp[4] : mp[2], *mbl = narrow ? mp[5] : mp[3];
             const int64_t ra = I.a_y, rb = I.b_z * a.nkp + I.b_y;
             for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
-                if (!mbar_wait_cluster(empty_bar(st), ph ^ 1u, abort_flag)) goto pair_producer_done;
-                mbar_arrive_expect_tx(full_bar(st), stage_tx);
+                if (!mbar_wait(empty_bar(st), ph ^ 1u, abort_flag)) goto pair_producer_done;
+                const uint32_t fb = leader ? full_bar(st) : map_to_rank(full_bar(st), 0);
+                if (leader) mbar_arrive_expect_tx(full_bar(st), pair_tx);
                 const uint32_t sbase = smem_u32(stages + size_t(st) * STAGE_BYTES_P);
                 const int64_t plane = kb * a.rows;
-                const int64_t oa = (plane + ra) * ROWB, ob = (plane + rb) * ROWB;
-                bulk_load(sbase, a.xa_h + oa, A_BYTES, full_bar(st));
-                bulk_load(sbase + A_BYTES, a.xa_l + oa, A_BYTES, full_bar(st));
-                bulk_load(sbase + 2 * A_BYTES, a.xb_h + ob, b_bytes, full_bar(st));
-                bulk_load(sbase + 2 * A_BYTES + BH_BYTES, a.xb_l + ob, b_bytes, full_bar(st));
+                const int32_t ya = static_cast<int32_t>((plane + ra) >> 3), yb = static_cast<int32_t>((plane + rb) >> 3);
+                tma_load_2d_pair(sbase, mp[0], 0, ya, fb);
+                tma_load_2d_pair(sbase + A_BYTES, mp[1], 0, ya, fb);
+                for (int j = 0; j < nbox; ++j) {
+                    tma_load_2d_pair(sbase + 2 * A_BYTES + j * 1024, mbh, 0, yb + 2 * j, fb);
+                    tma_load_2d_pair(sbase + 2 * A_BYTES + BH_BYTES + j * 1024, mbl, 0, yb + 2 * j, fb);
+                }
                 if (++st == STAGES_P) {
                     st = 0;
                     ph ^= 1u;
@@ -1084,8 +1103,8 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
             }
         }
     pair_producer_done:;
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------- MMA (leader) / relay (peer)
+    } else if (warp == 1 && lane == 0 && leader) {
+        // --------------------------------------------------------- MMA (leader)
         constexpr uint32_t idesc = (make_idesc<PREC>() & ~(0x1Fu << 24)) | (static_cast<uint32_t>((2 * BO) >> 4) << 24);
         int st = 0;
         uint32_t ph = 0, chain = 0;
@@ -1098,20 +1117,6 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
             if (item < 0) break;
             const Item I = decode_pair(a, item, static_cast<int>(cr));
             if (I.empty) continue;
-            if (!leader) {
-                for (int64_t kb = I.kb0; kb < I.kb1; ++kb) {
-                    if (!mbar_wait_cluster(full_bar(st), ph, abort_flag)) {
-                        aborted = true;
-                        break;
-                    }
-                    mbar_arrive_cluster(map_to_rank(full_bar(st), 0));
-                    if (++st == STAGES_P) {
-                        st = 0;
-                        ph ^= 1u;
-                    }
-                }
-                continue;
-            }
             const uint32_t idesc_i = (idesc & ~(0x3Fu << 17)) | (static_cast<uint32_t>(I.ncol >> 3) << 17);
             const int64_t sub_kb = a.sub_kb;
             for (int64_t kc = I.kb0; kc < I.kb1 && !aborted; kc += sub_kb) {
@@ -1124,7 +1129,7 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
                 tc_fence_after();
                 const uint32_t d = tmem_base + static_cast<uint32_t>(b * BF);
                 for (int64_t kb = kc; kb < kc1; ++kb) {
-                    if (!mbar_wait_cluster(full_bar(st), ph, abort_flag)) {
+                    if (!mbar_wait(full_bar(st), ph, abort_flag)) {
                         aborted = true;
                         break;
                     }
@@ -1155,7 +1160,7 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
                 ++chain;
             }
         }
-        if (leader && issued) {   // wait (bounded) until every MMA issued has completed
+        if (issued) {   // wait (bounded) until every MMA issued has completed
             tc_commit_pair(drain_bar, 1);
             int dummy = 0;
             volatile int *never = &dummy;
@@ -1199,7 +1204,7 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
             for (int j = 0; j < BF / 2; ++j) acc2[j] = 0.f;
             for (int64_t kc = kb0; kc < kb1; kc += sub_kb) {
                 const int b = chain & 1;
-                if (!mbar_wait_cluster(tfull_bar(b), (chain >> 1) & 1u, abort_flag)) {
+                if (!mbar_wait(tfull_bar(b), (chain >> 1) & 1u, abort_flag)) {
                     aborted = true;
                     break;
                 }
@@ -1287,10 +1292,17 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a) {
     }
 }
 
+// Maps: A hi / lo (16-row boxes: one 8 KB tile), B hi / lo (12-row boxes: a
+// full half tile of 6 KB), B hi / lo (2-row boxes of 1 KB, narrow tiles);
+// rows of 512 bytes.
 template <int PREC, bool X4>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
-    gram_pair_kernel(const __grid_constant__ GramArgs a) {
-    gram_pair_body<PREC, X4>(a);
+    gram_pair_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                     const __grid_constant__ CUtensorMap tmBhn, const __grid_constant__ CUtensorMap tmBln,
+                     const __grid_constant__ GramArgs a) {
+    const CUtensorMap *mp[NMAPS] = {&tmAh, &tmAl, &tmBh, &tmBl, &tmBhn, &tmBln};
+    gram_pair_body<PREC, X4>(a, mp);
 }
 
 constexpr int PREP_THREADS = 256;
@@ -2220,12 +2232,13 @@ cudaError_t launch_gram(const CUtensorMap *maps, const GramArgs &ga, int grid, c
 }
 
 template <int PREC, bool X4>
-cudaError_t launch_gram_pair(const GramArgs &ga, int grid, cudaStream_t st, int kind) {
+cudaError_t launch_gram_pair(const CUtensorMap *maps, const GramArgs &ga, int grid, cudaStream_t st, int kind) {
     cudaError_t e = cudaFuncSetAttribute(gram_pair_kernel<PREC, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(SMEM_TOTAL_P));
     if (e != cudaSuccess) return e;
     prof_begin(kind, st);
-    gram_pair_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL_P, st>>>(ga);
+    gram_pair_kernel<PREC, X4><<<grid, NTHREADS, SMEM_TOTAL_P, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
+                                                                      maps[5], ga);
     prof_end(st);
     return cudaGetLastError();
 }
@@ -2338,6 +2351,35 @@ cudaError_t launch_split_batch_class(int cls, const SplitDesc *d, int n, int64_t
 // instances, whose maps poly_setup encodes, touch them).
 int encode_maps(const GramLayout &, uint8_t *, int64_t, CUtensorMap *maps) {
     std::memset(maps, 0, sizeof(CUtensorMap) * NMAPS);
+    return TCORR_OK;
+}
+
+// CTA-pair kernel maps: each operand's tile images as a 2-D array of 512-byte
+// rows (8 tile rows each; 512 / esize elements per row), no swizzle (the
+// images are stored swizzled), boxes of 16 rows (A), 12 rows (full B half) and
+// 2 rows (narrow B halves in 1 KB steps).
+int encode_pair_maps(const GramLayout &L, uint8_t *base, CUtensorMap *maps) {
+    EncodeFn encode = get_encode();
+    if (!encode) return TCORR_EUNSUPPORTED;
+    const CUtensorMapDataType dt = L.prec == P_FP16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : L.prec == P_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t per_row = static_cast<cuuint64_t>(512 / L.esize);
+    const cuuint64_t n512 = static_cast<cuuint64_t>(L.Kp / L.bke) * static_cast<cuuint64_t>(L.rows) / 8;
+    const cuuint64_t dim[2] = {per_row, n512};
+    const cuuint64_t str[1] = {512};
+    const cuuint32_t es[2] = {1, 1};
+    uint8_t *bufs[4] = {base + L.off_xh, base + L.off_xl, base + (L.cross ? L.off_bh : L.off_xh),
+                        base + (L.cross ? L.off_bl : L.off_xl)};
+    const int buf_of[NMAPS] = {0, 1, 2, 3, 2, 3};
+    const cuuint32_t rows_of[NMAPS] = {16, 16, 12, 12, 2, 2};
+    for (int i = 0; i < NMAPS; ++i) {
+        const cuuint32_t box[2] = {static_cast<cuuint32_t>(per_row), rows_of[i]};
+        if (encode(&maps[i], dt, 2, bufs[buf_of[i]], dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled (pair)");
+    }
     return TCORR_OK;
 }
 
@@ -2708,13 +2750,16 @@ int gram_run_once(int kind, const float *d_x, int64_t T, int64_t N, int64_t tau_
     e = cudaMemsetAsync(ga.counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "work-item counter reset");
     if (L.pair) {   // one cluster of two CTAs per TPC
+        CUtensorMap pmaps[NMAPS];
+        const int prc = encode_pair_maps(L, ws, pmaps);
+        if (prc != TCORR_OK) return prc;
         const int64_t pairs = num_sms / 2;
         const int grid = 2 * static_cast<int>(ga.n_items < pairs ? ga.n_items : pairs);
         switch (L.prec * 2 + (L.x4 ? 1 : 0)) {
-            case P_FP16 * 2: e = launch_gram_pair<P_FP16, false>(ga, grid, st, kind & 1); break;
-            case P_BF16 * 2: e = launch_gram_pair<P_BF16, false>(ga, grid, st, kind & 1); break;
-            case P_BF16 * 2 + 1: e = launch_gram_pair<P_BF16, true>(ga, grid, st, kind & 1); break;
-            default: e = launch_gram_pair<P_TF32, false>(ga, grid, st, kind & 1); break;
+            case P_FP16 * 2: e = launch_gram_pair<P_FP16, false>(pmaps, ga, grid, st, kind & 1); break;
+            case P_BF16 * 2: e = launch_gram_pair<P_BF16, false>(pmaps, ga, grid, st, kind & 1); break;
+            case P_BF16 * 2 + 1: e = launch_gram_pair<P_BF16, true>(pmaps, ga, grid, st, kind & 1); break;
+            default: e = launch_gram_pair<P_TF32, false>(pmaps, ga, grid, st, kind & 1); break;
         }
         if (e != cudaSuccess) return cuda_fail(e, "gram_pair_kernel launch");
         e = launch_lag_reduce(L.p, ga.partial, finalize_args(kind, L, ws), d_out, st, w);
