@@ -127,11 +127,13 @@ void supertile_env(int64_t *rows, int64_t *cols) {
     }
 }
 
-// Band contraction on CTA pairs (gram_pair_kernel) for single instances;
-// TCORR_PAIR=0 / 1 overrides the default.
+// Band contraction on CTA pairs (gram_pair_kernel) for single instances:
+// TCORR_PAIR=0 / 1 first, then the tuned tile shape (tuned >= 0), then the
+// default (one-CTA tiles).
 constexpr bool kPairDefault = false;
-bool pair_enabled() {
+bool pair_enabled(int tuned) {
     if (const char *e = std::getenv("TCORR_PAIR")) return std::strcmp(e, "0") != 0;
+    if (tuned >= 0) return tuned != 0;
     return kPairDefault;
 }
 
@@ -827,6 +829,7 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             const GramArgs &a = *resolve(src, item, local, mp);
             int64_t kb0, kb1;
             int ncol;
+            float cs_pre = 1.f, rs_pre = 1.f;   // FP16 scales, requested before the sub-chains
             {
                 const Item I0 = decode_item(a, local);
                 if (I0.empty) {
@@ -838,6 +841,15 @@ __device__ __forceinline__ void gram_body(const Src &src) {
                 kb0 = I0.kb0;
                 kb1 = I0.kb1;
                 ncol = I0.ncol;
+                if (PREC == P_FP16) {
+                    const int64_t nscale = a.mode == 0 ? a.T : 3 * BO;
+                    const int64_t gofs = (I0.kb0 / a.kb_per_item) * a.scale_stride;
+                    if (et < BF) {
+                        const int64_t f = I0.sb0 + et * I0.sstr;
+                        cs_pre = f < nscale ? a.inv_scale_b[gofs + f] : 1.f;
+                    }
+                    if (row < I0.a_rows) rs_pre = a.inv_scale[gofs + I0.sa0 + row * I0.sstr];
+                }
             }
             // columns of this warp's half that the MMA wrote (the rest is stale and masked)
             const int hcols = ncol - (BF / 2) * half;
@@ -876,14 +888,8 @@ __device__ __forceinline__ void gram_body(const Src &src) {
             double *outp = a.partial + I.canon * WPG;
             float rs = 1.f;
             if (PREC == P_FP16) {
-                const int64_t nscale = a.mode == 0 ? a.T : 3 * BO;
-                const int64_t gofs = (I.kb0 / a.kb_per_item) * a.scale_stride;
-                const float *isc = a.inv_scale + gofs, *iscb = a.inv_scale_b + gofs;
-                for (int j = et; j < BF; j += 32 * NEPI) {
-                    const int64_t f = I.sb0 + j * I.sstr;
-                    cs[j] = f < nscale ? iscb[f] : 1.f;
-                }
-                rs = (row < I.a_rows) ? isc[I.sa0 + row * I.sstr] : 1.f;
+                if (et < BF) cs[et] = cs_pre;
+                rs = rs_pre;
                 named_bar_sync(1, 32 * NEPI);
             }
             // Diagonal sums of this warp's 32 x 96 block: entry (lane l, column jj)
@@ -1185,6 +1191,7 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a, const CUtensor
             if (item < 0) break;
             int64_t kb0, kb1;
             int ncol;
+            float cs_pre = 1.f, rs_pre = 1.f;   // FP16 scales, requested before the sub-chains
             {
                 const Item I0 = decode_pair(a, item, static_cast<int>(cr));
                 if (I0.empty) {
@@ -1196,6 +1203,14 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a, const CUtensor
                 kb0 = I0.kb0;
                 kb1 = I0.kb1;
                 ncol = I0.ncol;
+                if (PREC == P_FP16) {
+                    const int64_t gofs = (I0.kb0 / a.kb_per_item) * a.scale_stride;
+                    if (et < BF) {
+                        const int64_t f = I0.sb0 + et * I0.sstr;
+                        cs_pre = f < a.T ? a.inv_scale_b[gofs + f] : 1.f;
+                    }
+                    if (row < I0.a_rows) rs_pre = a.inv_scale[gofs + I0.sa0 + row * I0.sstr];
+                }
             }
             const int hcols = ncol - (BF / 2) * half;
             const int64_t sub_kb = a.sub_kb;
@@ -1233,13 +1248,8 @@ __device__ __forceinline__ void gram_pair_body(const GramArgs &a, const CUtensor
             double *outp = a.partial + I.canon * WPG;
             float rs = 1.f;
             if (PREC == P_FP16) {
-                const int64_t gofs = (I.kb0 / a.kb_per_item) * a.scale_stride;
-                const float *isc = a.inv_scale + gofs, *iscb = a.inv_scale_b + gofs;
-                for (int j = et; j < BF; j += 32 * NEPI) {
-                    const int64_t f = I.sb0 + j * I.sstr;
-                    cs[j] = f < a.T ? iscb[f] : 1.f;
-                }
-                rs = (row < I.a_rows) ? isc[I.sa0 + row * I.sstr] : 1.f;
+                if (et < BF) cs[et] = cs_pre;
+                rs = rs_pre;
                 named_bar_sync(1, 32 * NEPI);
             }
             // diagonal sums by warp shuffles, as in gram_body
@@ -2131,7 +2141,9 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->nkp = ceil_div(L->n_k + 2 * BO, 8) * 8;   // a tile starting at a real row never leaves its residue
     L->rows = s * L->nkp;
     L->T_pad = L->n_k * s;           // rows rho + k s for every rho < s, k < n_k exist
-    // kseg / sub_kb: tuning override, then environment, then tuned cache, then defaults
+    // kseg / sub_kb / supertile / tile shape: tuning override, then environment, then tuned
+    // cache, then defaults
+    int tuned_pair = -1;
     {
         const BandPlan p0 = make_band_plan(T, N, tau_max, s, BO, BF, 64, 1);
         const int64_t tiles = p0.n_res * p0.n_rows * p0.n_cols;
@@ -2144,6 +2156,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
         if (const int es = env_sub_kb()) c.sub_kb = es;
         L->kseg = c.kseg;
         L->sub_kb = c.sub_kb;
+        tuned_pair = c.pair;
         if (c.super_rows > 0 && c.super_cols > 0) {
             L->super_rows = c.super_rows;
             L->super_cols = c.super_cols;
@@ -2152,7 +2165,7 @@ bool make_layout(int64_t T, int64_t N, int64_t tau_max, int64_t s, int method, i
     L->p = make_band_plan(T, N, tau_max, s, BO, BF, L->kseg, 1);
     if (w) cap_origins(&L->p, w->orig_cap);
     L->p.WP = WPG;
-    L->pair = allow_pair && pair_enabled();
+    L->pair = allow_pair && pair_enabled(tuned_pair);
     if (L->pair) {   // an even number of row tiles; columns for the lags of both ranks of a pair
         L->p.pair = 1;
         L->p.n_rows = ceil_div(L->p.n_rows, 2) * 2;
@@ -2674,12 +2687,15 @@ size_t gram_workspace_size(int64_t T, int64_t N, int64_t tau_max, int64_t s, int
     GramLayout L;
     if (!make_layout(T, N, tau_max, s, method, kind, &L, w, true)) return 0;
     size_t need = L.total;
-    if (!w && tune_mode() != 0) {
-        const TuneChoice shortest{tune_min_kseg(), 0};
+    if (!w && tune_mode() != 0) {   // every candidate: the shortest item length, either tile shape
         const TuneChoice *prev = get_tune_override();
-        set_tune_override(&shortest);
-        GramLayout Ls;
-        if (make_layout(T, N, tau_max, s, method, kind, &Ls, nullptr, true) && Ls.total > need) need = Ls.total;
+        for (int pair : {0, 1}) {
+            TuneChoice shortest{tune_min_kseg(), 0};
+            shortest.pair = pair;
+            set_tune_override(&shortest);
+            GramLayout Ls;
+            if (make_layout(T, N, tau_max, s, method, kind, &Ls, nullptr, true) && Ls.total > need) need = Ls.total;
+        }
         set_tune_override(prev);
     }
     return need;

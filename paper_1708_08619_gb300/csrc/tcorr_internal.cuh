@@ -117,6 +117,7 @@ struct TuneChoice {
     int sub_kb;
     int super_rows = 0;
     int super_cols = 0;
+    int pair = -1;      // tile shape: 0 one CTA (M = 128), 1 a CTA pair (M = 256), -1 not chosen
 };
 // The default supertile (claim order) of the band kernel: 16 x 10 tiles.
 constexpr int kDefaultSuperRows = 16;

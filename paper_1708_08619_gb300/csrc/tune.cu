@@ -6,20 +6,22 @@
 //   supertile  -- the claim order of the band tiles: super_rows row tiles x
 //                 super_cols column tiles at a time, which sets how the ~152
 //                 items in flight share A and B rows in L2;
+//   tile shape -- 128 x 192 tiles on one CTA each, or 256 x 192 on a CTA pair
+//                 (cta_group::2, each CTA loading its A tile and half of B);
 //   sub_kb     -- K-blocks per TMEM accumulation sub-chain (longer chains
 //                 hand the accumulator over less often but lose more low bits).
-// kseg and the supertile are timed; sub_kb decides the accuracy, so the
+// kseg, the supertile and the tile shape are timed; sub_kb decides the accuracy, so the
 // candidates leave it at 0, which stands for the kind's default (a cached
 // nonzero sub_kb, written by hand or by an older library, is honoured).
 // Without TCORR_TUNE the library uses defaults measured on GB300
-// (tune_default_kseg and a 16 x 10 supertile).  With TCORR_TUNE=1 the first
+// (tune_default_kseg, a 16 x 10 supertile, one-CTA tiles).  With TCORR_TUNE=1 the first
 // call for a shape bucket times every candidate on the caller's stream (this
 // synchronises, so it is skipped while the stream is being captured) and
 // remembers the fastest; TCORR_TUNE=force re-times on every call.
 // TCORR_TUNE_CACHE names a file of JSON lines {"key": ..., "kseg": ...,
-// "sub_kb": ..., "super_rows": ..., "super_cols": ...} that is read at the
-// first lookup and appended to after each tuning run (lines without the
-// supertile fields are read with the default supertile).
+// "sub_kb": ..., "super_rows": ..., "super_cols": ..., "pair": ...} that is
+// read at the first lookup and appended to after each tuning run (lines
+// without the supertile or tile-shape fields are read with the defaults).
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -56,16 +58,17 @@ void load_cache_locked() {
     while (std::fgets(line, sizeof line, f)) {
         char key[256];
         long long kseg = 0;
-        int sub = 0, sr = 0, sc = 0;
+        int sub = 0, sr = 0, sc = 0, pr = -1;
         const int got = std::sscanf(line, " {\"key\": \"%255[^\"]\", \"kseg\": %lld, \"sub_kb\": %d, "
-                                          "\"super_rows\": %d, \"super_cols\": %d",
-                                    key, &kseg, &sub, &sr, &sc);
+                                          "\"super_rows\": %d, \"super_cols\": %d, \"pair\": %d",
+                                    key, &kseg, &sub, &sr, &sc, &pr);
         if (got >= 3 && kseg >= 64 && sub >= 0) {
             TuneChoice c{kseg, sub};
-            if (got == 5 && sr >= 1 && sc >= 1 && sr <= 4096 && sc <= 4096) {
+            if (got >= 5 && sr >= 1 && sc >= 1 && sr <= 4096 && sc <= 4096) {
                 c.super_rows = sr;
                 c.super_cols = sc;
             }
+            if (got == 6 && (pr == 0 || pr == 1)) c.pair = pr;
             g_tune[key] = c;
         }
     }
@@ -103,8 +106,9 @@ void tune_store(const std::string &key, const TuneChoice &c) {
     if (const char *path = std::getenv("TCORR_TUNE_CACHE")) {
         if (FILE *f = std::fopen(path, "a")) {
             std::fprintf(f, "{\"key\": \"%s\", \"kseg\": %lld, \"sub_kb\": %d, \"super_rows\": %d, "
-                            "\"super_cols\": %d}\n",
-                         key.c_str(), static_cast<long long>(c.kseg), c.sub_kb, c.super_rows, c.super_cols);
+                            "\"super_cols\": %d, \"pair\": %d}\n",
+                         key.c_str(), static_cast<long long>(c.kseg), c.sub_kb, c.super_rows, c.super_cols,
+                         c.pair < 0 ? 0 : c.pair);
             std::fclose(f);
         }
     }
@@ -114,13 +118,15 @@ const std::vector<TuneChoice> &tune_candidates() {
     static const std::vector<TuneChoice> c = [] {
         std::vector<TuneChoice> v;
         const int shapes[3][2] = {{16, 10}, {32, 5}, {8, 19}};
-        for (int64_t kseg : {4096, 8192, 16384})
-            for (const auto &sh : shapes) {
-                TuneChoice t{kseg, 0};
-                t.super_rows = sh[0];
-                t.super_cols = sh[1];
-                v.push_back(t);
-            }
+        for (int pair : {0, 1})
+            for (int64_t kseg : {4096, 8192, 16384})
+                for (const auto &sh : shapes) {
+                    TuneChoice t{kseg, 0};
+                    t.super_rows = sh[0];
+                    t.super_cols = sh[1];
+                    t.pair = pair;
+                    v.push_back(t);
+                }
         return v;
     }();
     return c;

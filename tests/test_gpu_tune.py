@@ -35,6 +35,7 @@ def test_tuner_times_candidates_once_and_persists(T, tmp_path, monkeypatch):
     # the accuracy-chosen default
     assert lines[0]["kseg"] in (4096, 8192, 16384) and lines[0]["sub_kb"] == 0
     assert (lines[0]["super_rows"], lines[0]["super_cols"]) in ((16, 10), (32, 5), (8, 19))
+    assert lines[0]["pair"] in (0, 1)               # the tile shape: one CTA or a CTA pair
     m2 = T.tcorr_msd(xd, 500, 1, "fp16x3").cpu().numpy()
     assert np.array_equal(m1, m2)                    # same tuned choice, no second tuning
     assert len(cache.read_text().splitlines()) == 1
@@ -90,3 +91,48 @@ def test_cache_lines_without_a_supertile_are_read(T, tmp_path):
     assert r.returncode == 0, r.stderr[-2000:]
     assert len(old.read_text().splitlines()) == 1          # the old line was used, no re-tuning
     assert np.isfinite(float(r.stdout.strip().splitlines()[-1]))
+
+
+_CHILD_SHA = """
+import sys, hashlib, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1708_08619_gb300 import build, synth, tcorr
+build.build(); tcorr.load()
+x = torch.from_numpy(synth.random_walk_positions(1200, 300, 0.01, 3.0, seed=34)).cuda()
+m = tcorr.tcorr_msd(x, 400, 1, "fp16x3").cpu().numpy()
+print(hashlib.sha256(m.tobytes()).hexdigest())
+"""
+
+
+def test_cached_tile_shape_selects_the_kernel(T, tmp_path):
+    """A cache line that chooses the CTA-pair tile shape runs the pair kernel:
+    its result is bit for bit that of TCORR_PAIR=1 with the same work-item
+    length and supertile, and differs in rounding from the one-CTA tiling."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = _CHILD_SHA.format(root=root)
+
+    def run(env_extra):
+        env = dict(os.environ, **env_extra)
+        for k in ("TCORR_PAIR", "TCORR_TUNE", "TCORR_TUNE_CACHE", "TCORR_KSEG", "TCORR_SUPER"):
+            if k not in env_extra:
+                env.pop(k, None)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return r.stdout.strip().splitlines()[-1]
+
+    probe = tmp_path / "probe.jsonl"
+    run({"TCORR_TUNE": "1", "TCORR_TUNE_CACHE": str(probe)})
+    key = json.loads(probe.read_text().splitlines()[0])["key"]
+    sha = {}
+    for pair in (0, 1):
+        cache = tmp_path / f"pair{pair}.jsonl"
+        cache.write_text(json.dumps({"key": key, "kseg": 4096, "sub_kb": 0, "super_rows": 16, "super_cols": 10,
+                                     "pair": pair}) + "\n")
+        sha[pair] = run({"TCORR_TUNE": "1", "TCORR_TUNE_CACHE": str(cache)})
+        assert len(cache.read_text().splitlines()) == 1      # the line was used, no re-tuning
+    forced = run({"TCORR_PAIR": "1", "TCORR_KSEG": "4096", "TCORR_SUPER": "16x10"})
+    assert sha[1] == forced
+    assert sha[0] != sha[1]
