@@ -395,89 +395,18 @@ def run_gpu(args, wl):
                 "issued_tflops": 3.0 * flops * issued_over_useful(N, T, tm, s) / msd_avg_s / 1e12,
                 "acf_kernel_frac": flops / acf_avg_s / 1e12 / peak_t}
 
-    # ---- the plain FP32 kernel on the same arrays, for the tensor-core vs plain comparison
-    plain_cmp = None
-    if method != "plain" and not args.no_plain_compare:
-        ws_p = torch.empty(max(tcorr.tcorr_workspace_size(T, N, tm, s, "plain"), 256), dtype=torch.uint8,
-                           device=dev)
-        reps = 2 if u_step < 1e13 else 1
-        tcorr.tcorr_profile_enable(True)
-        tcorr.tcorr_profile_read(0)
-        tcorr.tcorr_profile_read(1)
-        tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
-        tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
-        torch.cuda.synchronize()
-        pm_err = None
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tcorr.tcorr_profile_read(0)
-        tcorr.tcorr_profile_read(1)
-        e0.record(stream)
-        for _ in range(reps):
-            tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
-            tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pk_m = tcorr.tcorr_profile_read(0)
-        pk_c = tcorr.tcorr_profile_read(1)
-        tcorr.tcorr_profile_enable(False)
-        p_ms = e0.elapsed_time(e1) / reps
-        lane_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
-        pm_s = pk_m[0] / max(1, pk_m[1]) / 1e3
-        pc_s = pk_c[0] / max(1, pk_c[1]) / 1e3
-        m_plain, c_plain = out_m.cpu().numpy().copy(), out_c.cpu().numpy().copy()
-        plain_cmp = {"method": "plain", "ms_per_step_msd_acf": p_ms,
-                     "updates_per_s": u_step / (p_ms / 1000.0),
-                     "speedup_of_timed_method": value / (u_step / (p_ms / 1000.0)),
-                     "msd_kernel_ms": pm_s * 1e3, "acf_kernel_ms": pc_s * 1e3,
-                     "msd_lane_peak_frac": 6.0 * u_res / pm_s / lane_peak,
-                     "acf_lane_peak_frac": 3.0 * u_res / pc_s / lane_peak}
-        del ws_p
-    else:
-        m_plain = c_plain = None
-
-    # ---- host copies (pinned) of the inputs: the oracle reads them, the end-to-end steps upload them
+    # ---- host copies (pinned) of the inputs: the end-to-end steps upload them, the oracle reads them
     xh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
     vh = torch.empty((T, N, 3), dtype=torch.float32, pin_memory=True)
     xh.copy_(x)
     vh.copy_(v)
 
-    cpu = None
-    err_vs_oracle = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        lags = oracle_lags(wl)
-        m_ref, c_ref, el, n_up = oracle_pass(xh.numpy(), vh.numpy(), s, lags)
-        cores = oracle.default_threads()
-        # the same oracle on one host thread: the same lags, 1/cores of the atoms (the per-atom
-        # work is what the threads share), MSD only
-        n1 = max(64, N // max(1, cores))
-        x1 = np.ascontiguousarray(xh.numpy()[:, :n1, :])
-        t1 = time.perf_counter()
-        oracle.msd(x1, stride=s, lags=lags, nthreads=1)
-        el1 = time.perf_counter() - t1
-        del x1
-        r1 = int(sum(n1 * ((T - 1 - int(l)) // s + 1) for l in lags)) / el1
-        cpu = {"value": n_up / el, "unit": "updates/s", "cores": cores, "kind": "oracle",
-               "sample": f"MSD and VACF at {len(lags)} lags in [0, {tm}] (24 evenly spaced, 1, 2 and 16 "
-                         f"in the last 192), all atoms and origins of the same arrays; {el:.1f} s",
-               "value_1core": r1,
-               "sample_1core": f"MSD at the same {len(lags)} lags, the first {n1} atoms, one thread; "
-                               f"{el1:.1f} s"}
-        # the timed steps' results against the oracle at those lags (the metric's bar)
-        err_vs_oracle = {"lags": int(len(lags)),
-                         "msd_max_abs_over_msd_tau_max": float(np.max(np.abs(m_dev[lags] - m_ref)) / m_ref[-1]),
-                         "acf_max_abs_over_c0": float(np.max(np.abs(c_dev[lags] - c_ref)) / abs(c_ref[0])),
-                         "tolerance": 1e-6 if method == "plain" else 1e-5}
-        if m_plain is not None:
-            err_vs_oracle["plain_msd_max_rel_per_lag"] = float(
-                np.max(np.abs(m_plain[lags[1:]] - m_ref[1:]) / m_ref[1:])) if len(lags) > 1 else 0.0
-            err_vs_oracle["plain_acf_max_abs_over_c0"] = float(
-                np.max(np.abs(c_plain[lags] - c_ref)) / abs(c_ref[0]))
-            err_vs_oracle["plain_tolerance"] = 1e-6
-
-    # ---- end to end through the public API from pinned host memory: the device copies of the
-    # inputs and the workspace are released first (each variant allocates its own buffers)
-    del x, v, ws
+    # ---- end to end through the public API from pinned host memory, measured right after the
+    # timed steps and before the plain-kernel and oracle legs: the sustained load of those legs
+    # slowed host-to-device copies of these buffers (24-112 GB/s right after them, 211 GB/s
+    # before them).  The workspace is released first (each variant allocates its own buffers);
+    # the device inputs stay for the plain-kernel comparison that follows
+    del ws
     torch.cuda.empty_cache()
     m_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
     c_host = torch.empty(tm + 1, dtype=torch.float64, pin_memory=True)
@@ -613,6 +542,81 @@ def run_gpu(args, wl):
                 "h2d_gbs_measured": h2d_gbs,
                 "h2d_gbs_input_buffer": h2d_gbs_input,
                 "h2d_link_bound_ms": h2d / h2d_gbs / 1e6}
+
+    # ---- the plain FP32 kernel on the same arrays, for the tensor-core vs plain comparison
+    plain_cmp = None
+    if method != "plain" and not args.no_plain_compare:
+        ws_p = torch.empty(max(tcorr.tcorr_workspace_size(T, N, tm, s, "plain"), 256), dtype=torch.uint8,
+                           device=dev)
+        reps = 2 if u_step < 1e13 else 1
+        tcorr.tcorr_profile_enable(True)
+        tcorr.tcorr_profile_read(0)
+        tcorr.tcorr_profile_read(1)
+        tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
+        tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
+        torch.cuda.synchronize()
+        pm_err = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tcorr.tcorr_profile_read(0)
+        tcorr.tcorr_profile_read(1)
+        e0.record(stream)
+        for _ in range(reps):
+            tcorr.tcorr_msd(x, tm, s, "plain", out=out_m, ws=ws_p, stream=stream)
+            tcorr.tcorr_acf(v, tm, s, "plain", out=out_c, ws=ws_p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pk_m = tcorr.tcorr_profile_read(0)
+        pk_c = tcorr.tcorr_profile_read(1)
+        tcorr.tcorr_profile_enable(False)
+        p_ms = e0.elapsed_time(e1) / reps
+        lane_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+        pm_s = pk_m[0] / max(1, pk_m[1]) / 1e3
+        pc_s = pk_c[0] / max(1, pk_c[1]) / 1e3
+        m_plain, c_plain = out_m.cpu().numpy().copy(), out_c.cpu().numpy().copy()
+        plain_cmp = {"method": "plain", "ms_per_step_msd_acf": p_ms,
+                     "updates_per_s": u_step / (p_ms / 1000.0),
+                     "speedup_of_timed_method": value / (u_step / (p_ms / 1000.0)),
+                     "msd_kernel_ms": pm_s * 1e3, "acf_kernel_ms": pc_s * 1e3,
+                     "msd_lane_peak_frac": 6.0 * u_res / pm_s / lane_peak,
+                     "acf_lane_peak_frac": 3.0 * u_res / pc_s / lane_peak}
+        del ws_p
+    else:
+        m_plain = c_plain = None
+
+    cpu = None
+    err_vs_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        lags = oracle_lags(wl)
+        m_ref, c_ref, el, n_up = oracle_pass(xh.numpy(), vh.numpy(), s, lags)
+        cores = oracle.default_threads()
+        # the same oracle on one host thread: the same lags, 1/cores of the atoms (the per-atom
+        # work is what the threads share), MSD only
+        n1 = max(64, N // max(1, cores))
+        x1 = np.ascontiguousarray(xh.numpy()[:, :n1, :])
+        t1 = time.perf_counter()
+        oracle.msd(x1, stride=s, lags=lags, nthreads=1)
+        el1 = time.perf_counter() - t1
+        del x1
+        r1 = int(sum(n1 * ((T - 1 - int(l)) // s + 1) for l in lags)) / el1
+        cpu = {"value": n_up / el, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"MSD and VACF at {len(lags)} lags in [0, {tm}] (24 evenly spaced, 1, 2 and 16 "
+                         f"in the last 192), all atoms and origins of the same arrays; {el:.1f} s",
+               "value_1core": r1,
+               "sample_1core": f"MSD at the same {len(lags)} lags, the first {n1} atoms, one thread; "
+                               f"{el1:.1f} s"}
+        # the timed steps' results against the oracle at those lags (the metric's bar)
+        err_vs_oracle = {"lags": int(len(lags)),
+                         "msd_max_abs_over_msd_tau_max": float(np.max(np.abs(m_dev[lags] - m_ref)) / m_ref[-1]),
+                         "acf_max_abs_over_c0": float(np.max(np.abs(c_dev[lags] - c_ref)) / abs(c_ref[0])),
+                         "tolerance": 1e-6 if method == "plain" else 1e-5}
+        if m_plain is not None:
+            err_vs_oracle["plain_msd_max_rel_per_lag"] = float(
+                np.max(np.abs(m_plain[lags[1:]] - m_ref[1:]) / m_ref[1:])) if len(lags) > 1 else 0.0
+            err_vs_oracle["plain_acf_max_abs_over_c0"] = float(
+                np.max(np.abs(c_plain[lags] - c_ref)) / abs(c_ref[0]))
+            err_vs_oracle["plain_tolerance"] = 1e-6
+
 
     dtype = {"plain": "f32", "fp16x3": "f16x3 (f32 accumulate)", "bf16x3": "bf16x3 (f32 accumulate)",
              "bf16x4": "bf16x4 (f32 accumulate)", "tf32x3": "tf32x3 (f32 accumulate)"}.get(method, method)
