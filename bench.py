@@ -170,8 +170,8 @@ def gpu_identifier(torch, dev):
 # built now, per workload.  A capture too large for ncu is taken on the 1/8- or 1/16-atom case
 # of the same T and tau_max and scaled by the atom ratio: operand bytes, tiles and updates all
 # scale with N there.  A workload or method without an entry reports null.
-GRAM_TRAFFIC_BYTES = {("water", "fp16x3"): 8 * (1191.281536e6 + 3.768832e6),
-                      ("precision", "fp16x3"): 16 * (17071.781120e6 + 59.351808e6)}
+GRAM_TRAFFIC_BYTES = {("water", "fp16x3"): 8 * (1191.874304e6 + 3.766784e6),
+                      ("precision", "fp16x3"): 16 * (16901.152128e6 + 59.153920e6)}
 # DRAM bytes of one collective_kernel launch on the water-scale velocities (no reference frame):
 # ncu's dram__bytes.sum.per_second x gpu__time_duration.sum.
 COLLECTIVE_WATER_TRAFFIC_BYTES = 6.622334e12 * 594.496e-6
