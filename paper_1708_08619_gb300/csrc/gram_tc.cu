@@ -2806,8 +2806,12 @@ int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int
         cudaEventDestroy(e0);
         return TCORR_ECUDA;
     }
+    // A candidate that fails to launch (a launch-configuration error, which does not stick to the
+    // context) is skipped; the call fails only when no candidate runs, or on an error that
+    // stays with the context (every later candidate then fails too).
     float best_ms = -1.f;
-    int rc = TCORR_OK;
+    int rc = TCORR_OK, last_err = TCORR_OK;
+    bool sync_failed = false;
     for (const TuneChoice &c : tune_candidates()) {
         set_tune_override(&c);
         rc = gram_run_once(kind, d_x, T, N, tau_max, s, method, d_out, d_ws, ws_bytes, st, nullptr, d_y);   // warm-up
@@ -2817,9 +2821,13 @@ int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int
             cudaEventRecord(e1, st);
         }
         set_tune_override(nullptr);
-        if (rc != TCORR_OK) break;
+        if (rc != TCORR_OK) {
+            last_err = rc;
+            cudaGetLastError();
+            continue;
+        }
         if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = TCORR_ECUDA;
+            sync_failed = true;
             break;
         }
         float ms = 0.f;
@@ -2831,8 +2839,10 @@ int gram_tune(const std::string &key, int kind, const float *d_x, int64_t T, int
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == TCORR_OK) tune_store(key, *best);
-    return rc;
+    if (sync_failed) return TCORR_ECUDA;
+    if (best_ms < 0.f) return last_err != TCORR_OK ? last_err : TCORR_ECUDA;
+    tune_store(key, *best);
+    return TCORR_OK;
 }
 
 }  // namespace
