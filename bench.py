@@ -502,12 +502,13 @@ def run_gpu(args, wl):
 
     def e2e_hybrid():
         with torch.cuda.stream(copy_stream):
-            x2.copy_(xh, non_blocking=True)
+            for t, cx in zip(chunk_t, xcs):
+                x2[t:t + cx.shape[0]].copy_(cx, non_blocking=True)
             ev_x.record(copy_stream)
         sa.wait_event(ev_x)
         sb.wait_event(ev_x)
         tcorr.tcorr_msd(x2, tm, s, method, out=out_m, ws=ws, stream=sa)
-        tcorr.tcorr_acf_stream(vh, tm, s, method, chunk_frames=C, out=out_c, ws=ws_b, stream=sb)
+        tcorr.tcorr_acf_stream_chunks(vcs, tm, s, method, window_frames=C, out=out_c, ws=ws_b, stream=sb)
         stream.wait_stream(sa)
         stream.wait_stream(sb)
         finish_on(stream)
@@ -525,8 +526,8 @@ def run_gpu(args, wl):
         ev_go.record(stream)
         sa.wait_event(ev_go)
         sb.wait_event(ev_go)
-        tcorr.tcorr_msd_stream(xh, tm, s, method, chunk_frames=C, out=out_m, ws=ws_a, stream=sa)
-        tcorr.tcorr_acf_stream(vh, tm, s, method, chunk_frames=C, out=out_c, ws=ws_b, stream=sb)
+        tcorr.tcorr_msd_stream_chunks(xcs, tm, s, method, window_frames=C, out=out_m, ws=ws_a, stream=sa)
+        tcorr.tcorr_acf_stream_chunks(vcs, tm, s, method, window_frames=C, out=out_c, ws=ws_b, stream=sb)
         stream.wait_stream(sa)
         stream.wait_stream(sb)
         finish_on(stream)
@@ -550,10 +551,11 @@ def run_gpu(args, wl):
     e2e_value = u_step * world / e2e_s
     h2d = 2 * T * N * 3 * 4
     d2h = (3 * (tm + 1) + 2) * 8
-    e2e_api = {e2e_stream_s: "tcorr_msd_stream + tcorr_acf_stream on two streams, chunk_frames=%d" % C,
+    e2e_api = {e2e_stream_s: ("tcorr_msd_stream_chunks + tcorr_acf_stream_chunks (separately pinned 1 GiB frame "
+                              "chunks) on two streams, window_frames=%d" % C),
                e2e_incore_s: "host copies (separately pinned 1 GiB frame chunks) + tcorr_msd + tcorr_acf",
-               e2e_hybrid_s: ("positions copied whole + tcorr_msd, velocities through tcorr_acf_stream "
-                              "(chunk_frames=%d) behind them" % C)}
+               e2e_hybrid_s: ("positions copied in separately pinned 1 GiB frame chunks + tcorr_msd, velocities "
+                              "through tcorr_acf_stream_chunks (window_frames=%d) behind them" % C)}
     e2e_info = {"api": e2e_api[e2e_s],
                 "ms_per_step": e2e_s * 1e3,
                 "streamed_ms_per_step": e2e_stream_s * 1e3,
@@ -564,7 +566,7 @@ def run_gpu(args, wl):
                 "h2d_gbs_input_chunks": h2d_gbs_chunks,
                 "h2d_link_bound_ms": h2d / h2d_gbs / 1e6}
 
-    del xcs, vcs                          # the chunked host copies serve the in-core steps only
+    del xcs, vcs                          # the chunked host copies serve the end-to-end steps only
 
     # ---- the plain FP32 kernel on the same arrays, for the tensor-core vs plain comparison
     plain_cmp = None

@@ -334,6 +334,37 @@ int tcorr_acf_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, in
                      size_t ws_bytes, void *stream);
 
 /*
+ * The same streamed MSD / autocorrelation (Eq. 5 / Eq. 4, as tcorr_msd_stream
+ * and tcorr_acf_stream) for a trajectory held in host memory as consecutive
+ * chunks of frames: chunk i holds chunk_frames[i] frames as [frames][N][3]
+ * float32, and the trajectory is their concatenation (T = the sum).  The
+ * windows, copies and kernels are those of the one-array call, so the result
+ * is the same bit for bit; a window's new frames are copied from each chunk
+ * they touch.  Pinning the trajectory as separately allocated chunks of about
+ * 1 GiB keeps the host-to-device copies at the link's rate where one pinned
+ * allocation of many GB was measured several times slower after load on the
+ * host cores.
+ * h_chunks     : n_chunks host pointers, each 4-byte aligned and non-null; the
+ *                chunks must stay valid and unchanged until `stream` has finished.
+ * chunk_frames : n_chunks frame counts, each >= 1 (host array).
+ * n_chunks     : 1 .. 2^24.
+ * window_frames: as chunk_frames of tcorr_msd_stream (origins per window; 0 =
+ *                the default); the workspace is tcorr_stream_workspace_size(T,
+ *                N, tau_max, stride, method, window_frames) with T the total.
+ * Errors: as tcorr_msd_stream, plus TCORR_EINVAL for a null array, a null
+ * chunk pointer, n_chunks out of range or a chunk of fewer than one frame, and
+ * TCORR_EALIGN for a chunk pointer that is not 4-byte aligned.
+ */
+int tcorr_msd_stream_chunks(const float *const *h_chunks, const int64_t *chunk_frames, int n_chunks,
+                            int64_t N, int64_t tau_max, int64_t stride, int method,
+                            int64_t window_frames, double *d_out, void *d_ws, size_t ws_bytes,
+                            void *stream);
+int tcorr_acf_stream_chunks(const float *const *h_chunks, const int64_t *chunk_frames, int n_chunks,
+                            int64_t N, int64_t tau_max, int64_t stride, int method,
+                            int64_t window_frames, double *d_out, void *d_ws, size_t ws_bytes,
+                            void *stream);
+
+/*
  * Plain FP32 path without a caller workspace: the same result, bit for bit,
  * as tcorr_msd (kind 0) or tcorr_acf (kind 1) with method TCORR_PLAIN, but
  * the library allocates nothing and the caller passes no workspace.  The

@@ -143,13 +143,42 @@ struct StreamRes {
     }
 };
 
-int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
+// The host frames: one array, or consecutive chunks (chunk i holds frames
+// [first[i], first[i + 1]) as [frames][N][3] float32 rows).
+struct HostFrames {
+    const float *const *ptr;
+    const int64_t *first;     // n + 1 entries, first[0] = 0, first[n] = T
+    int n;
+};
+
+// Frames [f0, f0 + nf) into dst (rows of `row` bytes): one copy per chunk they touch.
+cudaError_t copy_frames(const HostFrames &H, int64_t K, int64_t f0, int64_t nf, float *dst, size_t row,
+                        cudaStream_t st) {
+    int i = 0;
+    while (i + 1 < H.n && H.first[i + 1] <= f0) ++i;
+    while (nf > 0) {
+        const int64_t in = f0 - H.first[i], take = H.first[i + 1] - f0 < nf ? H.first[i + 1] - f0 : nf;
+        const cudaError_t e = cudaMemcpyAsync(dst, H.ptr[i] + static_cast<size_t>(in) * K, take * row,
+                                              cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        dst += static_cast<size_t>(take) * K;
+        f0 += take;
+        nf -= take;
+        ++i;
+    }
+    return cudaSuccess;
+}
+
+int run_stream(int kind, const HostFrames &H, int64_t T, int64_t N, int64_t tau_max, int64_t s, int method,
                int64_t chunk, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
-    if (!h_x || !d_out) return TCORR_EINVAL;
+    if (!d_out) return TCORR_EINVAL;
     if (!corr_sizes_valid(T, N, tau_max, s) || method < TCORR_PLAIN || method > TCORR_AUTO || chunk < 0)
         return TCORR_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(h_x) & 3u) || (reinterpret_cast<uintptr_t>(d_out) & 7u) ||
-        (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+    for (int i = 0; i < H.n; ++i) {
+        if (!H.ptr[i]) return TCORR_EINVAL;
+        if (reinterpret_cast<uintptr_t>(H.ptr[i]) & 3u) return TCORR_EALIGN;
+    }
+    if ((reinterpret_cast<uintptr_t>(d_out) & 7u) || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
         return TCORR_EALIGN;
     StreamPlan P;
     if (!make_stream_plan(T, N, tau_max, s, method, chunk, &P)) return TCORR_EUNSUPPORTED;
@@ -182,8 +211,8 @@ int run_stream(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max
                 return cuda_fail(e, "halo copy");
         }
         if (Wc > have &&
-            (e = cudaMemcpyAsync(buf[b] + static_cast<size_t>(have) * P.K, h_x + static_cast<size_t>(t0 + have) * P.K,
-                                 (Wc - have) * row, cudaMemcpyHostToDevice, R.side)) != cudaSuccess)
+            (e = copy_frames(H, P.K, t0 + have, Wc - have, buf[b] + static_cast<size_t>(have) * P.K, row, R.side)) !=
+                cudaSuccess)
             return cuda_fail(e, "window copy");
         if ((e = cudaEventRecord(R.copied[b], R.side)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(st, R.copied[b], 0)) != cudaSuccess)
@@ -215,14 +244,57 @@ extern "C" size_t tcorr_stream_workspace_size(int64_t T, int64_t N, int64_t tau_
     return P.total;
 }
 
+namespace {
+
+int run_stream_one(int kind, const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride, int method,
+                   int64_t chunk_frames, double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!h_x) return TCORR_EINVAL;
+    const float *ptrs[1] = {h_x};
+    const int64_t first[2] = {0, T};
+    return run_stream(kind, HostFrames{ptrs, first, 1}, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws,
+                      ws_bytes, stream);
+}
+
+int run_stream_chunks(int kind, const float *const *h_chunks, const int64_t *chunk_frames, int n_chunks,
+                      int64_t N, int64_t tau_max, int64_t stride, int method, int64_t window_frames,
+                      double *d_out, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!h_chunks || !chunk_frames || n_chunks < 1 || n_chunks > (1 << 24)) return TCORR_EINVAL;
+    std::vector<int64_t> first(static_cast<size_t>(n_chunks) + 1, 0);
+    for (int i = 0; i < n_chunks; ++i) {
+        if (chunk_frames[i] < 1 || chunk_frames[i] > (int64_t(1) << 40)) return TCORR_EINVAL;
+        first[i + 1] = first[i] + chunk_frames[i];
+        if (first[i + 1] > (int64_t(1) << 40)) return TCORR_EINVAL;
+    }
+    return run_stream(kind, HostFrames{h_chunks, first.data(), n_chunks}, first[n_chunks], N, tau_max, stride,
+                      method, window_frames, d_out, d_ws, ws_bytes, stream);
+}
+
+}  // namespace
+
 extern "C" int tcorr_msd_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
                                 int method, int64_t chunk_frames, double *d_out, void *d_ws, size_t ws_bytes,
                                 void *stream) {
-    return run_stream(0, h_x, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws, ws_bytes, stream);
+    return run_stream_one(0, h_x, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws, ws_bytes, stream);
 }
 
 extern "C" int tcorr_acf_stream(const float *h_x, int64_t T, int64_t N, int64_t tau_max, int64_t stride,
                                 int method, int64_t chunk_frames, double *d_out, void *d_ws, size_t ws_bytes,
                                 void *stream) {
-    return run_stream(1, h_x, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws, ws_bytes, stream);
+    return run_stream_one(1, h_x, T, N, tau_max, stride, method, chunk_frames, d_out, d_ws, ws_bytes, stream);
+}
+
+extern "C" int tcorr_msd_stream_chunks(const float *const *h_chunks, const int64_t *chunk_frames, int n_chunks,
+                                       int64_t N, int64_t tau_max, int64_t stride, int method,
+                                       int64_t window_frames, double *d_out, void *d_ws, size_t ws_bytes,
+                                       void *stream) {
+    return run_stream_chunks(0, h_chunks, chunk_frames, n_chunks, N, tau_max, stride, method, window_frames, d_out,
+                             d_ws, ws_bytes, stream);
+}
+
+extern "C" int tcorr_acf_stream_chunks(const float *const *h_chunks, const int64_t *chunk_frames, int n_chunks,
+                                       int64_t N, int64_t tau_max, int64_t stride, int method,
+                                       int64_t window_frames, double *d_out, void *d_ws, size_t ws_bytes,
+                                       void *stream) {
+    return run_stream_chunks(1, h_chunks, chunk_frames, n_chunks, N, tau_max, stride, method, window_frames, d_out,
+                             d_ws, ws_bytes, stream);
 }

@@ -82,6 +82,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = [vp, i64, i64, i64, i64, ci, i64, vp, vp, sz, vp]
         f.restype = ci
+    for name in ("tcorr_msd_stream_chunks", "tcorr_acf_stream_chunks"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, vp, ci, i64, i64, i64, ci, i64, vp, vp, sz, vp]
+        f.restype = ci
     lib.tcorr_plain_static.argtypes = [ci, vp, i64, i64, i64, i64, vp, vp]
     lib.tcorr_plain_static.restype = ci
     lib.tcorr_profile_enable.argtypes = [ci]
@@ -449,6 +453,59 @@ def tcorr_acf_stream(x, tau_max: int, stride: int = 1, method=AUTO, chunk_frames
                      stream=None, device=None):
     """Autocorrelation of a host-resident A[T][N][3], streamed as tcorr_msd_stream."""
     return _corr_stream("tcorr_acf_stream", x, tau_max, stride, method, chunk_frames, out, ws, stream, device)
+
+
+def _corr_stream_chunks(fname: str, chunks, tau_max: int, stride: int, method, window_frames: int, out, ws,
+                        stream, device):
+    torch = _torch()
+    chunks = list(chunks)
+    if not chunks:
+        raise ValueError("chunks: at least one host tensor")
+    N = None
+    for c in chunks:
+        if not isinstance(c, torch.Tensor) or c.is_cuda:
+            raise TypeError("every chunk must be a host (CPU) torch tensor; pin each for overlapped copies")
+        if c.dtype != torch.float32 or c.dim() != 3 or c.shape[2] != 3 or not c.is_contiguous():
+            raise TypeError("every chunk must be a contiguous float32 tensor of shape [frames][N][3]")
+        if N is None:
+            N = c.shape[1]
+        elif c.shape[1] != N:
+            raise ValueError("chunks hold different atom counts")
+    T = sum(c.shape[0] for c in chunks)
+    m = _method(method)
+    device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = _held_by(torch.empty(tau_max + 1, dtype=torch.float64, device=device), stream)
+    _check_out(out, tau_max + 1, device)
+    _check_ws(ws, device)
+    need = tcorr_stream_workspace_size(T, N, tau_max, stride, m, window_frames)
+    if ws is None:
+        ws = _held_by(_alloc_ws(need, device), stream)
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    ptrs = (ctypes.c_void_p * len(chunks))(*[c.data_ptr() for c in chunks])
+    frames = (ctypes.c_int64 * len(chunks))(*[c.shape[0] for c in chunks])
+    rc = getattr(load(), fname)(ctypes.cast(ptrs, ctypes.c_void_p), ctypes.cast(frames, ctypes.c_void_p),
+                                len(chunks), N, tau_max, stride, m, window_frames, out.data_ptr(), ws_ptr,
+                                ws_bytes, _stream_ptr(stream))
+    if rc != 0:
+        raise TcorrError(rc, fname)
+    return out
+
+
+def tcorr_msd_stream_chunks(chunks, tau_max: int, stride: int = 1, method=AUTO, window_frames: int = 0, out=None,
+                            ws=None, stream=None, device=None):
+    """MSD of a host-resident trajectory given as consecutive frame chunks (host tensors
+    [frames][N][3], e.g. each pinned on its own), streamed as tcorr_msd_stream."""
+    return _corr_stream_chunks("tcorr_msd_stream_chunks", chunks, tau_max, stride, method, window_frames, out, ws,
+                               stream, device)
+
+
+def tcorr_acf_stream_chunks(chunks, tau_max: int, stride: int = 1, method=AUTO, window_frames: int = 0, out=None,
+                            ws=None, stream=None, device=None):
+    """Autocorrelation of a host-resident signal given as consecutive frame chunks."""
+    return _corr_stream_chunks("tcorr_acf_stream_chunks", chunks, tau_max, stride, method, window_frames, out, ws,
+                               stream, device)
 
 
 def tcorr_plain_static(kind: int, x, tau_max: int, stride: int = 1, out=None, stream=None):

@@ -283,6 +283,32 @@ def test_stream_workspace_holds_three_windows(lib):
     assert lib.tcorr_stream_workspace_size(T, N, tm, 1, 0, -1) == 0
 
 
+def call_msd_stream_chunks(lib, ptrs=(FAKE_X, FAKE_X + 0x10000), frames=(60, 40), n=None, N=10, tau_max=50, s=1,
+                           method=0, window=0, out=FAKE_OUT, ws=FAKE_WS, ws_bytes=0, null=None):
+    n = len(ptrs) if n is None else n
+    P = (ctypes.c_void_p * max(1, len(ptrs)))(*ptrs)
+    F = (ctypes.c_int64 * max(1, len(frames)))(*frames)
+    pa = None if null == "ptrs" else ctypes.cast(P, ctypes.c_void_p)
+    fa = None if null == "frames" else ctypes.cast(F, ctypes.c_void_p)
+    return lib.tcorr_msd_stream_chunks(pa, fa, n, N, tau_max, s, method, window, out, ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(null="ptrs"), dict(null="frames"), dict(n=0), dict(frames=(60, 0)), dict(ptrs=(FAKE_X, None)),
+    dict(out=None), dict(tau_max=100), dict(N=0), dict(s=0), dict(method=99), dict(window=-1),
+])
+def test_stream_chunks_invalid_arguments(lib, kw):
+    assert call_msd_stream_chunks(lib, **kw) == 1   # TCORR_EINVAL
+
+
+def test_stream_chunks_misaligned_and_workspace(lib):
+    assert call_msd_stream_chunks(lib, ptrs=(FAKE_X, FAKE_X + 0x10002)) == 2
+    assert call_msd_stream_chunks(lib, out=FAKE_OUT + 4) == 2
+    need = lib.tcorr_stream_workspace_size(100, 10, 50, 1, 0, 32)      # T = the chunks' total
+    assert need > 0
+    assert call_msd_stream_chunks(lib, window=32, ws_bytes=need - 1) == 4
+
+
 def call_xcf(lib, a=FAKE_X, b=FAKE_X + 0x1000, T=100, N=10, tau_max=50, s=1, method=0, out=FAKE_OUT,
              ws=FAKE_WS, ws_bytes=0):
     return lib.tcorr_xcf(a, b, T, N, tau_max, s, method, out, ws, ws_bytes, None)

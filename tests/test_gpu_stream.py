@@ -175,3 +175,27 @@ def test_stream_concurrent_with_incore_call_on_another_stream(T):
     check_vs_oracle(1, cc, oracle.acf(vh, stride=1, lags=lags), "fp16x3")
     assert np.array_equal(cc, alone)
     assert T.tcorr_status_poll() == 0
+
+
+@pytest.mark.parametrize("method", ["plain", "fp16x3"])
+def test_chunked_host_trajectory_equals_one_array(T, method):
+    """A trajectory held as separately pinned frame chunks (boundaries inside windows,
+    inside halos, one-frame chunks) streams to the same bits as the one-array call,
+    and the chunked calls refuse an empty chunk list before any work."""
+    rng = np.random.default_rng(91)
+    Tn, N, tm, s, window = 1500, 37, 400, 1, 256
+    x = (rng.normal(size=(Tn, N, 3)).cumsum(axis=0) * 0.1).astype(np.float32)
+    a = rng.normal(size=(Tn, N, 3)).astype(np.float32)
+    cuts = [0, 1, 2, 255, 700, 701, 1234, 1499, Tn]
+    for kind, arr in ((0, x), (1, a)):
+        whole = streamed(T, kind, arr, tm, s, method, window)
+        chunks = [torch.from_numpy(np.ascontiguousarray(arr[c0:c1])).pin_memory()
+                  for c0, c1 in zip(cuts[:-1], cuts[1:])]
+        f = T.tcorr_msd_stream_chunks if kind == 0 else T.tcorr_acf_stream_chunks
+        for _ in range(2):
+            got = f(chunks, tm, s, method, window_frames=window)
+            torch.cuda.synchronize()
+            assert np.array_equal(got.cpu().numpy(), whole), (kind, method)
+    with pytest.raises(ValueError):
+        T.tcorr_msd_stream_chunks([], tm, s, method)
+    assert T.tcorr_status_poll() == 0
